@@ -1,0 +1,354 @@
+"""Circuit-time benchmark on one GB300 (or N replicas under torchrun).
+
+One step = one full execution of a kernelized circuit on a 2^n complex64
+state already resident in HBM (all kernels of the plan, back to back on one
+stream).  The workload is the mixed-gate circuit generator at 30 qubits:
+5000 gates drawn uniformly from {H, X, RX, RZ, CX, CZ, CP, SWAP}, partner
+distance 1 + Geom(0.3), seed 100 -- an 8 GiB state, larger than L2, so no
+L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  `value` is milliseconds per circuit over the
+whole job (max-over-ranks elapsed time / circuits executed by all ranks).
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "circuit time and HBM-roofline fraction at 30 qubits, FP32 vs fused 3xTF32+learned plan"
+N_QUBITS = 30
+N_GATES = 5000
+SEED = 100
+WORKLOAD = (f"mixed circuit, {N_QUBITS} qubits, {N_GATES} gates from {{H,X,RX,RZ,CX,CZ,CP,SWAP}}, "
+            f"partner distance 1+Geom(0.3), seed {SEED}; complex64 state 8 GiB")
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def mem_available_gib():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) / (1 << 20)
+    except Exception:
+        pass
+    return 0.0
+
+
+def oracle_sample(gates, budget_s, n_full=N_QUBITS):
+    """Times the FP64 oracle, gate by gate, on a bounded prefix of the
+    circuit.  Runs at n_full qubits when host memory allows (16 GiB complex128
+    at 30 qubits), else at 28 qubits scaled by the state-size ratio.
+    Returns (ms per circuit estimate, sample description, threads)."""
+    import numpy as np
+    from oracle import sim
+    n = n_full
+    if mem_available_gib() < (16 << (n - 30)) * 1.0 + 8:
+        n = 28
+    scale = 2.0 ** (n_full - n)
+    sub = gates.copy()
+    ok = (sub["q0"] < n) & ((sub["q1"] < n))
+    sub = sub[ok]
+    psi = sim.zero_state(n)
+    done, t0 = 0, time.perf_counter()
+    el = 0.0
+    while done < len(sub) and el < budget_s:
+        psi = _apply_inplace(sim, n, sub[done:done + 1], psi)
+        done += 1
+        el = time.perf_counter() - t0
+    per_gate_ms = el * 1e3 / max(done, 1) * scale
+    desc = (f"first {done} gates of the circuit on a {n}-qubit complex128 state"
+            + (f", scaled x{scale:.0f} to {n_full} qubits" if scale != 1 else "")
+            + f"; per-gate time x {len(gates)} gates")
+    del psi
+    return per_gate_ms * len(gates), desc, sim.threads()
+
+
+def _apply_inplace(sim, n, g, psi):
+    import ctypes
+    import numpy as np
+    from synth.circuits import GATE_DTYPE
+    gg = np.ascontiguousarray(g, dtype=GATE_DTYPE)
+    f = psi.view(np.float64)
+    rc = sim.lib().or_apply_circuit(n, f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    gg.ctypes.data_as(ctypes.c_void_p), len(gg))
+    if rc != 0:
+        raise RuntimeError("oracle rejected a gate")
+    return psi
+
+
+def reference_arm(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from synth import circuits as C
+    gates = C.mixed_circuit(N_QUBITS, N_GATES, SEED)
+    step_budget = 4.0
+    for _ in range(args.warmup):
+        oracle_sample(gates, 0.5)
+    vals, desc, thr = [], "", 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, desc, thr = oracle_sample(gates, step_budget)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms/circuit",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": wall * 1e3 / max(args.steps, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": N_GATES,
+                   "plan": "none (FP64 oracle applies gates one at a time)"},
+        "cpu_baseline": {"value": value, "unit": "ms/circuit", "cores": thr, "kind": "oracle",
+                         "sample": desc + f"; {step_budget:.0f} s per step"},
+        "e2e": {"value": value, "unit": "ms/circuit", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def make_plan(Q, gates, which):
+    if which == "A":
+        opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, cost_kind=Q.QS_COST_ANALYTIC,
+                              precision=Q.QS_PREC_FP32, shm_max_active=13, fuse_kmax=0)
+        label = "A: analytic-cost OrderedKernelize, shared-memory kernels, FP32"
+    else:
+        raise ValueError(which)
+    return Q.Plan(N_QUBITS, gates, opts), label
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plan", default="A")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local)) \
+            if "device_id" in dist.init_process_group.__code__.co_varnames else dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2408_09055_gb300 import qsim as Q
+    from synth import circuits as C
+
+    gates = C.mixed_circuit(N_QUBITS, N_GATES, SEED)
+    plan, label = make_plan(Q, gates, args.plan)
+    ps = plan.stats()
+    kdesc = [plan.kernel(k) for k in range(ps.num_kernels)]
+    n = N_QUBITS
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    st = Q.State(n, buf.data_ptr())
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    st.set_zero(sp)
+    for _ in range(args.warmup):
+        st.run(plan, sp)
+    torch.cuda.synchronize()
+    timer = Q.Timer(plan, args.steps)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st.run_timed(plan, timer, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    per_kernel_ms, runs = timer.read()
+    norm = st.norm2(sp)
+
+    # roofline of the dominant kernel type (algorithmic bytes = one read and
+    # one write of the state per launch)
+    pass_bytes = 16.0 * (1 << n)
+    by_type = {}
+    for k, d in enumerate(kdesc):
+        nm = "shm_kernel_v1" if d.type == Q.QS_KERNEL_SHM else "fused_fp32_kernel"
+        t = by_type.setdefault(nm, [0.0, 0])
+        t[0] += per_kernel_ms[k]
+        t[1] += runs
+    dom = max(by_type, key=lambda x: by_type[x][0])
+    avg_ms = by_type[dom][0] / max(by_type[dom][1], 1)
+    hbm, _, src = peaks()
+    achieved = pass_bytes / (avg_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "launches_timed": by_type[dom][1], "avg_launch_ms": avg_ms,
+            "share_of_step": by_type[dom][0] / max(sum(v[0] for v in by_type.values()), 1e-12)}
+
+    # end to end through the public API: H2D of the input state from pinned
+    # memory, the circuit, D2H of the output state
+    host_in = torch.zeros(2 << n, dtype=torch.float32).pin_memory()
+    host_in[0] = 1.0
+    host_out = torch.empty(2 << n, dtype=torch.float32).pin_memory()
+    hin = host_in.numpy().view(np.complex64)
+    hout = host_out.numpy().view(np.complex64)
+    e2e_steps = max(1, min(args.steps, 3))
+    st.write(hin, stream=sp)
+    st.run(plan, sp)
+    st.read(out=hout, stream=sp)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st.write(hin, stream=sp)
+        st.run(plan, sp)
+        st.read(out=hout, stream=sp)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_norm = float(np.sum(np.abs(hout.astype(np.complex128)) ** 2))
+
+    value = elapsed_ms / (args.steps * world)
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms/circuit", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": n, "gates": N_GATES, "plan": label,
+                   "kernels": int(ps.num_kernels), "shm_kernels": int(ps.num_shm),
+                   "fused_kernels": int(ps.num_fused), "passes": int(ps.num_kernels),
+                   "planner_ms": ps.planner_ms, "l2": "no flush: the 8 GiB state exceeds L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gates_per_s": N_GATES / (value * 1e-3),
+        "hbm_roofline_frac_circuit": ps.num_kernels * pass_bytes / (value * 1e-3) / 1e9 / hbm,
+        "roofline": roof,
+        "gpu_launches": int(sum(v[1] for v in by_type.values())) * 1,
+        "clocks": clk,
+        "norm2_after": norm,
+        "e2e": {"value": e2e_ms / (e2e_steps * world) if world == 1 else e2e_ms / e2e_steps / world,
+                "unit": "ms/circuit", "steps": e2e_steps,
+                "h2d_bytes_per_step": int(8 << n), "d2h_bytes_per_step": int(8 << n),
+                "norm2_out": e2e_norm},
+    }
+    del host_in, host_out
+    if rank == 0 and not args.no_cpu_baseline:
+        v, desc, thr = oracle_sample(gates, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "ms/circuit", "cores": thr, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * qsim -- GB300 (sm_103a) state-vector execution of kernelized circuits.
+ *
+ * C ABI of libqsim.so.  Every entry point returns an int status (QS_OK = 0,
+ * negative on error; qs_strerror() names it) unless stated otherwise.  No
+ * C++ exception crosses this boundary and nothing aborts the process.
+ * Device pointers are plain CUDA device addresses of the current device;
+ * host pointers are ordinary process memory.  `stream` arguments are
+ * cudaStream_t values passed as void* (NULL = the legacy default stream).
+ *
+ * Conventions (Sec. 2 of the paper, Eq. 1): qubit q is bit q of the
+ * amplitude index; a state of n qubits is 2^n complex64 amplitudes stored
+ * interleaved (re, im) as float pairs.  For a two-qubit gate, q[0] is the
+ * less significant bit of its 4x4 matrix index; CX has its control on q[0].
+ *
+ * Threading: a qs_plan is immutable after qs_plan_circuit and may be used
+ * from several threads; a qs_state must not be used concurrently.
+ */
+#ifndef QSIM_H_
+#define QSIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QS_OK 0
+#define QS_EINVAL (-1)       /* bad argument (size, qubit index, null pointer) */
+#define QS_ENOMEM (-2)       /* device or pinned host allocation failed */
+#define QS_EUNSUPPORTED (-3) /* valid request this build does not implement */
+#define QS_ETIMEDOUT (-4)    /* a bounded wait ran out (host or device) */
+#define QS_ECUDA (-5)        /* a CUDA runtime call failed */
+#define QS_EPLAN (-6)        /* planning failed or a plan is inconsistent */
+
+const char* qs_strerror(int status);
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* qs_last_cuda_error(void);
+
+/* ---- circuit ------------------------------------------------------------
+ * Gate set of the paper's benchmark workloads.  Matrices (the paper names
+ * the gates without writing them; OpenQASM 2 conventions):
+ *   H, X, RX(t)=exp(-i t X/2), RZ(t)=exp(-i t Z/2),
+ *   U3(t,p,l)=[[cos t/2, -e^{il} sin t/2],[e^{ip} sin t/2, e^{i(p+l)} cos t/2]],
+ *   CX (control q[0]), CZ, CP(t)=diag(1,1,1,e^{it}), SWAP,
+ *   RXX(t)=exp(-i t X(x)X/2).
+ * Insular qubits (Definition 2): RZ, CZ and CP are diagonal in all their
+ * qubits; CX's control is insular.  X is treated as non-insular.          */
+enum qs_gate_type {
+  QS_H = 0, QS_X = 1, QS_RX = 2, QS_RZ = 3, QS_U3 = 4,
+  QS_CX = 5, QS_CZ = 6, QS_CP = 7, QS_SWAP = 8, QS_RXX = 9,
+  QS_NUM_GATE_TYPES = 10
+};
+
+typedef struct qs_gate {
+  int32_t type;  /* enum qs_gate_type */
+  int32_t nq;    /* 1 or 2; must match the type */
+  int32_t q[2];  /* qubits; q[1] unused (-1) for one-qubit gates */
+  double p[3];   /* angles: RX/RZ/CP/RXX use p[0]; U3 uses p[0..2] */
+} qs_gate;       /* 40 bytes */
+
+/* ---- planning (Partition / Kernelize, Sec. 4-5, Alg. 3-5) ---------------- */
+enum qs_algo {
+  QS_ALGO_PER_GATE = 0,  /* one kernel per gate (test baseline)                 */
+  QS_ALGO_GREEDY = 1,    /* greedy packing into fusion kernels of <= fuse_kmax
+                            qubits (the paper's greedy baseline, Sec. 6.4)       */
+  QS_ALGO_ORDERED = 2,   /* OrderedKernelize: optimal contiguous segmentation,
+                            O(|C|^2) (Alg. 5)                                    */
+  QS_ALGO_KERNELIZE = 3  /* Kernelize DP over ordered kernel sets with the
+                            extensible-qubit state reduction (Alg. 3, Alg. 4)
+                            and the optimisations of Appendix A.2            */
+};
+enum qs_cost_kind { QS_COST_ANALYTIC = 0, QS_COST_LEARNED = 1 };
+enum qs_precision {
+  QS_PREC_FP32 = 0,   /* fused unitaries on CUDA cores, FP32                 */
+  QS_PREC_TF32 = 1,   /* fused unitaries on tensor cores, one TF32 product   */
+  QS_PREC_TF32X3 = 2  /* split-precision 3xTF32 on tensor cores              */
+};
+enum qs_kernel_type { QS_KERNEL_SHM = 0, QS_KERNEL_FUSED = 1 };
+
+/* Analytic cost ("Cost Function in Kernelize"): a shared-memory kernel costs
+ * alpha + sum of gate_cost[type]; a fused kernel on k qubits costs
+ * fuse_cost[k].  Units are arbitrary but shared (microseconds measured on
+ * the target GPU for the default table).                                    */
+typedef struct qs_cost_table {
+  double alpha;
+  double gate_cost[QS_NUM_GATE_TYPES];
+  double fuse_cost[16]; /* index = qubit count; entries above fuse_kmax unused */
+} qs_cost_table;
+
+typedef struct qs_mlp qs_mlp; /* learned cost model, see below */
+
+typedef struct qs_plan_opts {
+  int32_t algo;           /* enum qs_algo                                      */
+  int32_t cost_kind;      /* enum qs_cost_kind; LEARNED needs `mlp`            */
+  int32_t precision;      /* enum qs_precision of fused kernels                */
+  int32_t shm_max_active; /* max |A| of a shared-memory kernel, 1..14          */
+  int32_t forced_low;     /* low qubits forced into every shared-memory kernel
+                             (the paper forces 3 for complex128; 4 = 128 B
+                             runs of complex64)                                */
+  int32_t fuse_kmin;      /* fused kernels narrower than this are widened     */
+  int32_t fuse_kmax;      /* widest fused kernel; 0 disables fusion            */
+  int32_t prune_T;        /* Kernelize pruning threshold T (<= 0: no pruning)  */
+  int32_t attach_single;  /* Kernelize: attach one-qubit gates to neighbours   */
+  int32_t local_qubits;   /* L: qubits resident on the GPU per chunk (0 = n)   */
+  const qs_cost_table* cost; /* NULL: built-in table                           */
+  const qs_mlp* mlp;         /* learned cost model (cost_kind = LEARNED)        */
+} qs_plan_opts;
+
+/* Fills `opts` with the defaults (Kernelize, analytic cost, FP32, |A| <= 12,
+ * 4 forced low qubits, fused k in [1, 6], T = 500, attach on, L = n).       */
+void qs_plan_opts_default(qs_plan_opts* opts);
+/* The built-in analytic cost table. */
+void qs_cost_table_default(qs_cost_table* out);
+
+typedef struct qs_plan qs_plan;
+
+/* Partition + Kernelize a circuit of `ngates` gates on `n` qubits (1..40).
+ * The gate array is copied; the plan is owned by the caller and released
+ * with qs_plan_free.  Errors: QS_EINVAL (bad gate, qubit or option),
+ * QS_EPLAN (no feasible kernelization), QS_ENOMEM.                          */
+int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates,
+                    const qs_plan_opts* opts, qs_plan** out);
+void qs_plan_free(qs_plan* plan);
+
+typedef struct qs_plan_stats {
+  int32_t n;
+  int32_t num_stages;
+  uint64_t num_gates;
+  uint64_t num_kernels;
+  uint64_t num_shm;
+  uint64_t num_fused;
+  double cost;        /* total model cost (Eq. 2)                           */
+  double planner_ms;  /* host time spent in qs_plan_circuit                 */
+  uint64_t dp_states; /* Kernelize: largest DP frontier                    */
+} qs_plan_stats;
+int qs_plan_stats_get(const qs_plan* plan, qs_plan_stats* out);
+
+typedef struct qs_kernel_desc {
+  int32_t type;       /* enum qs_kernel_type                                 */
+  int32_t stage;      /* stage index                                        */
+  int32_t nqubits;    /* |A| (shm) or k (fused), widening included          */
+  int32_t num_gates;
+  uint64_t qubit_mask;/* physical qubits of A (shm) or of the fused targets */
+  double cost;
+} qs_kernel_desc;
+int qs_plan_kernel(const qs_plan* plan, uint64_t k, qs_kernel_desc* out);
+/* Copies the circuit indices of kernel k's gates, in execution order, into
+ * ids[0..cap); returns the count or a negative status.                     */
+int64_t qs_plan_kernel_gates(const qs_plan* plan, uint64_t k, int32_t* ids, uint64_t cap);
+/* The fused kernel's unitary in FP64, row-major complex interleaved,
+ * 2^k x 2^k, index bit j = the j-th lowest qubit of qubit_mask.            */
+int qs_plan_fused_matrix(const qs_plan* plan, uint64_t k, double* out, uint64_t cap_doubles);
+/* Checks Theorem 2 on a plan: every gate exactly once and, for every pair of
+ * gates sharing a qubit that is not insular in both, circuit order kept.
+ * QS_OK or QS_EPLAN.                                                        */
+int qs_plan_validate(const qs_plan* plan, const qs_gate* gates, uint64_t ngates);
+
+/* ---- state ---------------------------------------------------------------- */
+typedef struct qs_state qs_state;
+
+/* A state of n qubits (1..34) in device memory.  With device_ptr == NULL the
+ * library allocates 2^n * 8 bytes (cudaMalloc) and frees it in
+ * qs_state_free; otherwise the caller's buffer (>= 2^n * 8 bytes, 16-byte
+ * aligned) is used and stays owned by the caller.  Contents are undefined
+ * until qs_state_set_zero or qs_write_amplitudes.                          */
+int qs_state_create(int32_t n, void* device_ptr, qs_state** out);
+void qs_state_free(qs_state* st);
+void* qs_state_device_ptr(const qs_state* st);
+int qs_state_set_zero(qs_state* st, void* stream); /* |0...0> */
+
+/* Applies the plan to the state, stream-ordered and asynchronous.  The first
+ * call with a plan uploads its kernel programs (device allocation).  Errors
+ * found asynchronously surface at the next synchronising call.             */
+int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream);
+
+/* Per-kernel timing with CUDA events on the launching stream (used by the
+ * benchmark for the roofline of each kernel type).  A timer holds
+ * (num_kernels + 1) * max_runs events; qs_run_plan_timed records one event
+ * before every kernel and one after the last, on `stream`.
+ * qs_timer_read synchronises the events and writes, for every kernel of the
+ * plan, the sum over recorded runs of its duration in ms (per_kernel_ms
+ * has num_kernels entries) and the number of runs.                          */
+typedef struct qs_timer qs_timer;
+int qs_timer_create(const qs_plan* plan, uint64_t max_runs, qs_timer** out);
+int qs_run_plan_timed(const qs_plan* plan, qs_state* st, qs_timer* timer, void* stream);
+int qs_timer_read(qs_timer* timer, double* per_kernel_ms, uint64_t cap, uint64_t* runs);
+void qs_timer_free(qs_timer* timer);
+
+/* Copy amplitudes [first, first+count) between the state and host memory
+ * (interleaved float pairs).  Synchronises the stream.                      */
+int qs_read_amplitudes(const qs_state* st, uint64_t first, uint64_t count,
+                       float* host_out, void* stream);
+int qs_write_amplitudes(qs_state* st, uint64_t first, uint64_t count,
+                        const float* host_in, void* stream);
+
+/* a8: reductions accumulated in FP64.  norm2 = sum |a_i|^2.  With a
+ * reference state ref (2^n complex128, device memory, interleaved):
+ * fidelity = |<ref|psi>|^2 / (<ref|ref> <psi|psi>), maxabs = max_i |ref_i -
+ * psi_i|.  Synchronise the stream.                                          */
+int qs_state_norm2(const qs_state* st, double* out, void* stream);
+int qs_state_compare_c128(const qs_state* st, const double* ref_device,
+                          double* fidelity, double* maxabs, void* stream);
+
+/* ---- low-level device operations (each cites its step) ------------------ */
+
+/* a6: out[pi(i)] = in[i] where pi moves bit j of i to bit perm[j]
+ * (perm a permutation of 0..n-1).  Out of place; in and out must not
+ * overlap.                                                                   */
+int qs_remap(const float* in_device, float* out_device, int32_t n,
+             const int32_t* perm, void* stream);
+
+/* Applies one fused 2^k x 2^k unitary (row-major complex64 on the host,
+ * index bit j = qubit targets[j]) to a device state, in the given precision.
+ * A direct entry to the fused-kernel path (a5).                             */
+int qs_apply_fused(float* state_device, int32_t n, const int32_t* targets,
+                   int32_t k, const float* u_host, int32_t precision, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H_ */

@@ -1,0 +1,482 @@
+// C ABI of libqsim (include/qsim.h): plans, states, execution (Alg. 1's
+// Partition / Execute on one GPU).
+#include <algorithm>
+#include <bit>
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "internal.hpp"
+
+namespace qs {
+
+static thread_local std::string g_last_cuda;
+
+void set_cuda_error(const char* what, cudaError_t e) {
+  g_last_cuda = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return QS_OK;
+  set_cuda_error("cuda", e);
+  return e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA;
+}
+
+// Uploads every kernel program of the plan to the current device (once per
+// device; later calls reuse it).
+static int ensure_device(PlanImpl* p, DeviceCache** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::lock_guard<std::mutex> lk(p->mu);
+  for (auto& d : p->dev)
+    if (d.device == dev) {
+      *out = &d;
+      return QS_OK;
+    }
+  DeviceCache dc;
+  dc.device = dev;
+  std::vector<uint8_t> host;
+  for (size_t i = 0; i < p->kernels.size(); ++i) {
+    uint64_t off = (host.size() + 255) & ~uint64_t(255);
+    host.resize(off);
+    dc.op_off.push_back(off);
+    if (p->kernels[i].type == QS_KERNEL_SHM) {
+      const auto& ops = p->shm[i].ops;
+      host.resize(off + ops.size() * sizeof(DevOp));
+      if (!ops.empty()) std::memcpy(host.data() + off, ops.data(), ops.size() * sizeof(DevOp));
+    } else {
+      const auto& u = p->fused[i].u;
+      host.resize(off + u.size() * sizeof(float));
+      std::memcpy(host.data() + off, u.data(), u.size() * sizeof(float));
+    }
+  }
+  if (host.empty()) host.resize(256);
+  e = cudaMalloc(&dc.buf, host.size());
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemcpy(dc.buf, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dc.buf);
+    return cuda_status(e);
+  }
+  p->dev.push_back(std::move(dc));
+  *out = &p->dev.back();
+  return QS_OK;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+const char* qs_strerror(int s) {
+  switch (s) {
+    case QS_OK: return "ok";
+    case QS_EINVAL: return "invalid argument";
+    case QS_ENOMEM: return "out of memory";
+    case QS_EUNSUPPORTED: return "unsupported";
+    case QS_ETIMEDOUT: return "timed out";
+    case QS_ECUDA: return "CUDA error";
+    case QS_EPLAN: return "planning failed or invalid plan";
+    default: return "unknown status";
+  }
+}
+
+const char* qs_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+void qs_cost_table_default(qs_cost_table* t) {
+  if (!t) return;
+  std::memset(t, 0, sizeof(*t));
+  // Microseconds per kernel on a 30-qubit state (GB300): alpha = one
+  // read+write pass of 16 GiB at HBM speed; per-gate costs and fused costs
+  // from the calibration runs of the timing generator.
+  t->alpha = 2600.0;
+  const double dense1 = 60.0, diag = 40.0, dense2 = 120.0;
+  t->gate_cost[QS_H] = dense1;
+  t->gate_cost[QS_X] = dense1;
+  t->gate_cost[QS_RX] = dense1;
+  t->gate_cost[QS_U3] = dense1;
+  t->gate_cost[QS_RZ] = diag;
+  t->gate_cost[QS_CZ] = diag;
+  t->gate_cost[QS_CP] = diag;
+  t->gate_cost[QS_CX] = dense1;
+  t->gate_cost[QS_SWAP] = dense2;
+  t->gate_cost[QS_RXX] = dense2;
+  const double fuse[16] = {0, 2700, 2700, 2700, 2800, 3200, 5200, 10400,
+                           20800, 41600, 83200, 166400, 332800, 665600, 1331200, 2662400};
+  std::memcpy(t->fuse_cost, fuse, sizeof(fuse));
+}
+
+void qs_plan_opts_default(qs_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->algo = QS_ALGO_ORDERED;
+  o->cost_kind = QS_COST_ANALYTIC;
+  o->precision = QS_PREC_FP32;
+  o->shm_max_active = 12;
+  o->forced_low = 4;
+  o->fuse_kmin = 1;
+  o->fuse_kmax = 6;
+  o->prune_T = 500;
+  o->attach_single = 1;
+  o->local_qubits = 0;
+  o->cost = nullptr;
+  o->mlp = nullptr;
+}
+
+int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_plan_opts* opts,
+                    qs_plan** out) {
+  if (!out) return QS_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > kMaxQubits || (ngates > 0 && !gates)) return QS_EINVAL;
+  qs_plan_opts o;
+  if (opts) o = *opts; else qs_plan_opts_default(&o);
+  if (o.shm_max_active < 1 || o.shm_max_active > kMaxShmActive) return QS_EINVAL;
+  if (o.forced_low < 0 || o.forced_low > o.shm_max_active) return QS_EINVAL;
+  if (o.fuse_kmax < 0 || o.fuse_kmax > kMaxFuse) return QS_EINVAL;
+  if (o.fuse_kmin < 0 || (o.fuse_kmax > 0 && o.fuse_kmin > o.fuse_kmax)) return QS_EINVAL;
+  if (o.precision < QS_PREC_FP32 || o.precision > QS_PREC_TF32X3) return QS_EINVAL;
+  if (o.algo < QS_ALGO_PER_GATE || o.algo > QS_ALGO_KERNELIZE) return QS_EINVAL;
+  if (o.cost_kind == QS_COST_LEARNED && !o.mlp) return QS_EINVAL;
+  if (o.cost_kind != QS_COST_ANALYTIC && o.cost_kind != QS_COST_LEARNED) return QS_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  qs_plan* p = new (std::nothrow) qs_plan();
+  if (!p) return QS_ENOMEM;
+  PlanImpl& P = p->impl;
+  P.n = n;
+  P.opts = o;
+  if (o.cost) P.cost = *o.cost; else qs_cost_table_default(&P.cost);
+  P.opts.cost = nullptr;
+  try {
+    P.gates.resize(ngates);
+    for (uint64_t i = 0; i < ngates; ++i) {
+      int rc = make_gate(gates[i], n, &P.gates[i]);
+      if (rc != QS_OK) {
+        delete p;
+        return rc;
+      }
+    }
+    int rc = plan_kernels(&P);
+    if (rc == QS_OK) rc = compile_programs(&P);
+    if (rc == QS_OK) rc = validate_plan(&P);
+    if (rc != QS_OK) {
+      delete p;
+      return rc;
+    }
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return QS_ENOMEM;
+  } catch (...) {
+    delete p;
+    return QS_EPLAN;
+  }
+  P.planner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return QS_OK;
+}
+
+void qs_plan_free(qs_plan* p) {
+  if (!p) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  for (auto& d : p->impl.dev) {
+    if (d.buf) {
+      cudaSetDevice(d.device);
+      cudaFree(d.buf);
+    }
+  }
+  if (cur >= 0 && !p->impl.dev.empty()) cudaSetDevice(cur);
+  delete p;
+}
+
+int qs_plan_stats_get(const qs_plan* p, qs_plan_stats* s) {
+  if (!p || !s) return QS_EINVAL;
+  const PlanImpl& P = p->impl;
+  std::memset(s, 0, sizeof(*s));
+  s->n = P.n;
+  s->num_stages = 1;
+  s->num_gates = P.gates.size();
+  s->num_kernels = P.kernels.size();
+  for (const auto& k : P.kernels) (k.type == QS_KERNEL_SHM ? s->num_shm : s->num_fused)++;
+  s->cost = P.total_cost;
+  s->planner_ms = P.planner_ms;
+  s->dp_states = P.dp_states;
+  return QS_OK;
+}
+
+int qs_plan_kernel(const qs_plan* p, uint64_t k, qs_kernel_desc* out) {
+  if (!p || !out || k >= p->impl.kernels.size()) return QS_EINVAL;
+  const Kernel& K = p->impl.kernels[k];
+  out->type = K.type;
+  out->stage = K.stage;
+  out->nqubits = std::popcount(K.mask);
+  out->num_gates = (int32_t)K.gates.size();
+  out->qubit_mask = K.mask;
+  out->cost = K.cost;
+  return QS_OK;
+}
+
+int64_t qs_plan_kernel_gates(const qs_plan* p, uint64_t k, int32_t* ids, uint64_t cap) {
+  if (!p || k >= p->impl.kernels.size()) return QS_EINVAL;
+  const Kernel& K = p->impl.kernels[k];
+  if (ids) {
+    if (cap < K.gates.size()) return QS_EINVAL;
+    std::copy(K.gates.begin(), K.gates.end(), ids);
+  }
+  return (int64_t)K.gates.size();
+}
+
+int qs_plan_fused_matrix(const qs_plan* p, uint64_t k, double* out, uint64_t cap) {
+  if (!p || !out || k >= p->impl.kernels.size()) return QS_EINVAL;
+  if (p->impl.kernels[k].type != QS_KERNEL_FUSED) return QS_EINVAL;
+  const auto& u = p->impl.fused[k].u64;
+  if (cap < u.size()) return QS_EINVAL;
+  std::copy(u.begin(), u.end(), out);
+  return QS_OK;
+}
+
+int qs_plan_validate(const qs_plan* p, const qs_gate* gates, uint64_t ngates) {
+  if (!p) return QS_EINVAL;
+  const PlanImpl& P = p->impl;
+  if (ngates != P.gates.size() || (ngates && !gates)) return QS_EPLAN;
+  for (uint64_t i = 0; i < ngates; ++i) {
+    Gate g;
+    if (make_gate(gates[i], P.n, &g) != QS_OK) return QS_EPLAN;
+    const Gate& h = P.gates[i];
+    if (g.type != h.type || g.q0 != h.q0 || g.q1 != h.q1) return QS_EPLAN;
+  }
+  return validate_plan(&P);
+}
+
+int qs_state_create(int32_t n, void* device_ptr, qs_state** out) {
+  if (!out) return QS_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > 34) return QS_EINVAL;
+  if (device_ptr && (reinterpret_cast<uintptr_t>(device_ptr) & 15)) return QS_EINVAL;
+  qs_state* s = new (std::nothrow) qs_state();
+  if (!s) return QS_ENOMEM;
+  s->n = n;
+  if (device_ptr) {
+    s->psi = static_cast<float2*>(device_ptr);
+  } else {
+    size_t bytes = sizeof(float2) << n;
+    cudaError_t e = cudaMalloc(&s->psi, bytes);
+    if (e != cudaSuccess) {
+      delete s;
+      return cuda_status(e);
+    }
+    s->owned = true;
+  }
+  *out = s;
+  return QS_OK;
+}
+
+void qs_state_free(qs_state* s) {
+  if (!s) return;
+  if (s->owned && s->psi) cudaFree(s->psi);
+  delete s;
+}
+
+void* qs_state_device_ptr(const qs_state* s) { return s ? s->psi : nullptr; }
+
+int qs_state_set_zero(qs_state* s, void* stream) {
+  if (!s) return QS_EINVAL;
+  return launch_set_zero(s->psi, s->n, (cudaStream_t)stream);
+}
+
+struct qs_timer {
+  const qs_plan* plan = nullptr;
+  uint64_t max_runs = 0, runs = 0;
+  std::vector<cudaEvent_t> ev;  // (nk + 1) per run
+};
+
+static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_timer* tm);
+
+int qs_timer_create(const qs_plan* plan, uint64_t max_runs, qs_timer** out) {
+  if (!plan || !out || max_runs == 0) return QS_EINVAL;
+  *out = nullptr;
+  qs_timer* t = new (std::nothrow) qs_timer();
+  if (!t) return QS_ENOMEM;
+  t->plan = plan;
+  t->max_runs = max_runs;
+  const uint64_t per = plan->impl.kernels.size() + 1;
+  t->ev.assign(per * max_runs, nullptr);
+  for (auto& e : t->ev) {
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) {
+      qs_timer_free(t);
+      return cuda_status(r);
+    }
+  }
+  *out = t;
+  return QS_OK;
+}
+
+void qs_timer_free(qs_timer* t) {
+  if (!t) return;
+  for (auto e : t->ev)
+    if (e) cudaEventDestroy(e);
+  delete t;
+}
+
+int qs_run_plan_timed(const qs_plan* plan, qs_state* st, qs_timer* t, void* stream) {
+  if (!t || t->plan != plan) return QS_EINVAL;
+  if (t->runs >= t->max_runs) return QS_EINVAL;
+  return run_plan_impl(plan, st, stream, t);
+}
+
+int qs_timer_read(qs_timer* t, double* per_kernel_ms, uint64_t cap, uint64_t* runs) {
+  if (!t || !runs) return QS_EINVAL;
+  const uint64_t nk = t->plan->impl.kernels.size();
+  if (nk && (!per_kernel_ms || cap < nk)) return QS_EINVAL;
+  for (uint64_t k = 0; k < nk; ++k) per_kernel_ms[k] = 0;
+  for (uint64_t r = 0; r < t->runs; ++r) {
+    for (uint64_t k = 0; k < nk; ++k) {
+      float ms = 0;
+      cudaEvent_t a = t->ev[r * (nk + 1) + k], b = t->ev[r * (nk + 1) + k + 1];
+      cudaError_t e = cudaEventSynchronize(b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess) return cuda_status(e);
+      per_kernel_ms[k] += ms;
+    }
+  }
+  *runs = t->runs;
+  return QS_OK;
+}
+
+int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream) {
+  return run_plan_impl(plan, st, stream, nullptr);
+}
+
+static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_timer* tm) {
+  if (!plan || !st) return QS_EINVAL;
+  PlanImpl* P = const_cast<PlanImpl*>(&plan->impl);
+  if (P->n != st->n) return QS_EINVAL;
+  DeviceCache* dc = nullptr;
+  int rc = ensure_device(P, &dc);
+  if (rc != QS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t* ev = tm ? &tm->ev[tm->runs * (P->kernels.size() + 1)] : nullptr;
+  for (size_t i = 0; i < P->kernels.size(); ++i) {
+    const Kernel& K = P->kernels[i];
+    if (ev) {
+      cudaError_t e = cudaEventRecord(ev[i], s);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    const uint8_t* base = static_cast<const uint8_t*>(dc->buf) + dc->op_off[i];
+    if (K.type == QS_KERNEL_SHM) {
+      const ShmProgram& sp = P->shm[i];
+      ShmLaunch a;
+      a.psi = st->psi;
+      a.n = P->n;
+      a.m = sp.m;
+      std::copy(sp.act, sp.act + kMaxShmActive, a.act);
+      a.ops = reinterpret_cast<const DevOp*>(base);
+      a.nops = (int)sp.ops.size();
+      rc = launch_shm(a, s);
+    } else {
+      const FusedProgram& fp = P->fused[i];
+      FusedLaunch a;
+      a.psi = st->psi;
+      a.n = P->n;
+      a.k = fp.k;
+      std::copy(fp.targets, fp.targets + kMaxFuse, a.targets);
+      a.u = reinterpret_cast<const float2*>(base);
+      a.precision = P->opts.precision;
+      rc = launch_fused(a, s);
+    }
+    if (rc != QS_OK) return rc;
+  }
+  if (ev) {
+    cudaError_t e = cudaEventRecord(ev[P->kernels.size()], s);
+    if (e != cudaSuccess) return cuda_status(e);
+    tm->runs++;
+  }
+  return QS_OK;
+}
+
+static int copy_amps(void* dst, const void* src, uint64_t first, uint64_t count, int n,
+                     cudaMemcpyKind kind, cudaStream_t s) {
+  if (count == 0) return QS_OK;
+  if (first > (1ull << n) || count > (1ull << n) - first) return QS_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(float2), kind, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+int qs_read_amplitudes(const qs_state* st, uint64_t first, uint64_t count, float* host_out,
+                       void* stream) {
+  if (!st || (!host_out && count)) return QS_EINVAL;
+  return copy_amps(host_out, st->psi + first, first, count, st->n, cudaMemcpyDeviceToHost,
+                   (cudaStream_t)stream);
+}
+
+int qs_write_amplitudes(qs_state* st, uint64_t first, uint64_t count, const float* host_in,
+                        void* stream) {
+  if (!st || (!host_in && count)) return QS_EINVAL;
+  return copy_amps(st->psi + first, host_in, first, count, st->n, cudaMemcpyHostToDevice,
+                   (cudaStream_t)stream);
+}
+
+int qs_state_norm2(const qs_state* st, double* out, void* stream) {
+  if (!st || !out) return QS_EINVAL;
+  return launch_norm2(st->psi, st->n, out, (cudaStream_t)stream);
+}
+
+int qs_state_compare_c128(const qs_state* st, const double* ref, double* fid, double* maxabs,
+                          void* stream) {
+  if (!st || !ref || !fid || !maxabs) return QS_EINVAL;
+  return launch_compare(st->psi, reinterpret_cast<const double2*>(ref), st->n, fid, maxabs,
+                        (cudaStream_t)stream);
+}
+
+int qs_remap(const float* in, float* out, int32_t n, const int32_t* perm, void* stream) {
+  if (!in || !out || !perm || n < 1 || n > 34) return QS_EINVAL;
+  uint64_t seen = 0;
+  for (int j = 0; j < n; ++j) {
+    if (perm[j] < 0 || perm[j] >= n || ((seen >> perm[j]) & 1)) return QS_EINVAL;
+    seen |= 1ull << perm[j];
+  }
+  const uint64_t bytes = sizeof(float2) << n;
+  const char* a = reinterpret_cast<const char*>(in);
+  const char* b = reinterpret_cast<const char*>(out);
+  if (a < b + bytes && b < a + bytes) return QS_EINVAL;
+  return launch_remap(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), n, perm,
+                      (cudaStream_t)stream);
+}
+
+int qs_apply_fused(float* state, int32_t n, const int32_t* targets, int32_t k, const float* u_host,
+                   int32_t precision, void* stream) {
+  if (!state || !targets || !u_host || k < 1 || k > kMaxFuse || n < k || n > 34) return QS_EINVAL;
+  if (precision < QS_PREC_FP32 || precision > QS_PREC_TF32X3) return QS_EINVAL;
+  uint64_t seen = 0;
+  for (int j = 0; j < k; ++j) {
+    if (targets[j] < 0 || targets[j] >= n || ((seen >> targets[j]) & 1)) return QS_EINVAL;
+    seen |= 1ull << targets[j];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(float2) << (2 * k);
+  void* du = nullptr;
+  cudaError_t e = cudaMallocAsync(&du, bytes, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemcpyAsync(du, u_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(du, s);
+    return cuda_status(e);
+  }
+  FusedLaunch a;
+  a.psi = reinterpret_cast<float2*>(state);
+  a.n = n;
+  a.k = k;
+  std::fill(a.targets, a.targets + kMaxFuse, -1);
+  std::copy(targets, targets + k, a.targets);
+  a.u = static_cast<const float2*>(du);
+  a.precision = precision;
+  int rc = launch_fused(a, s);
+  cudaFreeAsync(du, s);
+  if (rc == QS_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  return rc;
+}
+
+}  // extern "C"

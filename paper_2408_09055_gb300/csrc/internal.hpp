@@ -1,0 +1,140 @@
+// Internal types shared by the planner (host C++) and the CUDA kernels of
+// libqsim.  Not part of the public ABI (see include/qsim.h).
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "qsim.h"
+
+namespace qs {
+
+constexpr int kMaxQubits = 40;
+constexpr int kMaxShmActive = 14;  // 2^14 complex64 = 128 KiB tile
+constexpr int kMaxFuse = 7;        // widest fused unitary (2^7 x 2^7)
+
+// ---- gates ---------------------------------------------------------------
+struct Gate {
+  int32_t type = 0, nq = 1, q0 = 0, q1 = -1;
+  double p[3] = {0, 0, 0};
+  uint64_t qmask = 0;   // all qubits of the gate
+  uint64_t nimask = 0;  // non-insular qubits (Definition 2)
+};
+
+int gate_arity(int type);
+// Fills m (row-major, complex interleaved, 2^nq x 2^nq) with the gate matrix.
+void gate_matrix(const Gate& g, double* m);
+// Validates a public gate and fills the internal one.  Returns QS_OK/EINVAL.
+int make_gate(const qs_gate& in, int n, Gate* out);
+bool gate_is_diagonal(int type);
+
+// ---- plan ----------------------------------------------------------------
+struct Kernel {
+  int32_t type = QS_KERNEL_SHM;
+  int32_t stage = 0;
+  std::vector<int32_t> gates;  // circuit indices, execution order
+  uint64_t mask = 0;           // shm: active set; fused: target set (widened)
+  double cost = 0;
+};
+
+// One device op of a shared-memory kernel program (see shm kernel).
+enum : uint8_t { OP_DENSE1 = 0, OP_DENSE2 = 1, OP_DIAG = 2 };
+struct alignas(16) DevOp {
+  uint8_t kind;
+  int8_t t0, t1;   // local bits (DENSE: targets; DIAG: qubit 0/1 if active, else -1)
+  int8_t g0, g1;   // DIAG: physical bit of qubit 0/1 when not active, else -1
+  uint8_t pad[3];
+  uint32_t cloc;   // local control bits, all must be 1
+  uint32_t pad2;
+  uint64_t cglob;  // physical control bits of the batch, all must be 1
+  float m[32];     // DENSE1: 2x2 complex; DENSE2: 4x4 complex; DIAG: 4 complex entries
+};
+static_assert(sizeof(DevOp) == 160, "DevOp layout");
+
+struct ShmProgram {
+  int m = 0;                 // |A|
+  int act[kMaxShmActive];    // physical qubit of local bit j (ascending)
+  std::vector<DevOp> ops;
+};
+
+struct FusedProgram {
+  int k = 0;
+  int targets[kMaxFuse];     // physical qubit of matrix index bit j
+  std::vector<float> u;      // 2^k x 2^k complex64, row-major interleaved
+  std::vector<double> u64;   // the FP64 product (kept for export / tests)
+};
+
+struct DeviceCache {
+  int device = -1;
+  void* buf = nullptr;       // ops + matrices of every kernel
+  std::vector<uint64_t> op_off;  // byte offset of kernel i's ops / matrix
+};
+
+struct PlanImpl {
+  int n = 0;
+  std::vector<Gate> gates;
+  qs_plan_opts opts{};
+  qs_cost_table cost{};
+  std::vector<Kernel> kernels;
+  std::vector<ShmProgram> shm;      // indexed like kernels (empty for fused)
+  std::vector<FusedProgram> fused;  // indexed like kernels (empty for shm)
+  double planner_ms = 0, total_cost = 0;
+  uint64_t dp_states = 0;
+  std::mutex mu;
+  std::vector<DeviceCache> dev;     // one per device the plan ran on
+};
+
+// ---- planner (planner.cpp) --------------------------------------------------
+struct CostModel {
+  const PlanImpl* plan;
+  double fusion(uint64_t qmask) const;                  // INF if infeasible
+  double shm(uint64_t nimask, double gate_cost_sum) const;
+  double gate_cost(int type) const { return plan->cost.gate_cost[type]; }
+};
+int plan_kernels(PlanImpl* p);         // fills p->kernels
+int compile_programs(PlanImpl* p);     // fills p->shm / p->fused
+int validate_plan(const PlanImpl* p);  // Theorem 2 check
+
+// ---- device side (kernels_*.cu) ----------------------------------------------
+struct ShmLaunch {
+  float2* psi;
+  int n, m;
+  int act[kMaxShmActive];
+  const DevOp* ops;
+  int nops;
+};
+int launch_shm(const ShmLaunch& a, cudaStream_t s);
+
+struct FusedLaunch {
+  float2* psi;
+  int n, k;
+  int targets[kMaxFuse];
+  const float2* u;  // device, 2^k x 2^k
+  int precision;
+};
+int launch_fused(const FusedLaunch& a, cudaStream_t s);
+
+int launch_set_zero(float2* psi, int n, cudaStream_t s);
+int launch_norm2(const float2* psi, int n, double* out_host, cudaStream_t s);
+int launch_compare(const float2* psi, const double2* ref, int n, double* fid,
+                   double* maxabs, cudaStream_t s);
+int launch_remap(const float2* in, float2* out, int n, const int32_t* perm, cudaStream_t s);
+
+int cuda_status(cudaError_t e);  // records the message, maps to QS_ECUDA
+void set_cuda_error(const char* what, cudaError_t e);
+
+}  // namespace qs
+
+struct qs_plan {
+  qs::PlanImpl impl;
+};
+struct qs_state {
+  int n = 0;
+  float2* psi = nullptr;
+  bool owned = false;
+};

@@ -1,0 +1,180 @@
+"""GPU parity: plans executed by libqsim's CUDA kernels against the FP64
+oracle, element by element (fidelity >= 1 - 1e-6, max-abs <= 1e-5)."""
+import numpy as np
+import pytest
+
+from oracle import sim
+from synth import circuits as C
+from tests.gpu_util import assert_close_state, need_gpu, run_plan_on_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = {"per_gate": 0, "greedy": 1, "ordered": 2}
+
+
+def gen(kind, n, seed):
+    if kind == "layered":
+        return C.layered_u3_cz(n, 6, seed)
+    if kind == "mixed":
+        return C.mixed_circuit(n, 400, seed)
+    return C.entangling_circuit(n, 4, seed)
+
+
+@pytest.mark.parametrize("kind", ["layered", "mixed", "entangling"])
+@pytest.mark.parametrize("algo", list(ALGOS))
+@pytest.mark.parametrize("n", [12, 17])
+def test_shm_plans_match_oracle(kind, algo, n):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    g = gen(kind, n, n)
+    plan = Q.Plan(n, g, algo=ALGOS[algo], fuse_kmax=0)
+    assert plan.validate() == 0
+    got, _, _ = run_plan_on_gpu(n, plan)
+    assert_close_state(got, sim.apply(n, g))
+
+
+@pytest.mark.parametrize("kmax", [3, 5, 6, 7])
+def test_fused_fp32_plans_match_oracle(kmax):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 16
+    g = C.entangling_circuit(n, 4, 11)
+    cost = Q.default_cost_table()
+    for k in range(16):
+        cost.fuse_cost[k] = 1.0  # make every feasible fusion cheaper than shm
+    plan = Q.Plan(n, g, algo=2, fuse_kmax=kmax, fuse_kmin=kmax, cost=cost, precision=Q.QS_PREC_FP32)
+    st = plan.stats()
+    assert st.num_fused > 0
+    got, _, _ = run_plan_on_gpu(n, plan)
+    assert_close_state(got, sim.apply(n, g))
+
+
+def test_random_input_state_and_mixed_kernel_types():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 15
+    rng = np.random.default_rng(5)
+    psi0 = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 /= np.linalg.norm(psi0)
+    psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    g = C.mixed_circuit(n, 600, 5)
+    plan = Q.Plan(n, g, algo=2, fuse_kmax=5)
+    got, _, _ = run_plan_on_gpu(n, plan, psi0)
+    assert_close_state(got, sim.apply(n, g, psi0))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 9])
+def test_tiny_states(n):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    g = C.mixed_circuit(n, 50, n) if n >= 2 else C.make_gates([(C.H, 0), (C.RZ, 0, None, 0.3), (C.U3, 0, None, 1, 2, 3)])
+    for algo in (0, 2):
+        plan = Q.Plan(n, g, algo=algo, fuse_kmax=min(n, 4))
+        got, _, _ = run_plan_on_gpu(n, plan)
+        assert_close_state(got, sim.apply(n, g))
+
+
+def test_empty_circuit_is_identity():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 10
+    plan = Q.Plan(n, C.make_gates([]))
+    assert plan.stats().num_kernels == 0
+    got, _, _ = run_plan_on_gpu(n, plan)
+    ref = np.zeros(1 << n, dtype=complex); ref[0] = 1
+    assert np.array_equal(got, ref.astype(np.complex64))
+
+
+def test_closed_forms_on_gpu():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 20
+    plan = Q.Plan(n, C.ghz(n))
+    got, _, _ = run_plan_on_gpu(n, plan)
+    ref = np.zeros(1 << n, dtype=complex); ref[0] = ref[-1] = 2 ** -0.5
+    assert_close_state(got, ref)
+    x = 0xABCDE
+    g = C.concat(C.basis_prep(n, x), C.qft(n))
+    got, _, _ = run_plan_on_gpu(n, Q.Plan(n, g))
+    y = np.arange(1 << n)
+    assert_close_state(got, np.exp(2j * np.pi * x * y / (1 << n)) / 2 ** (n / 2))
+
+
+def test_norm_and_compare_reductions():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 18
+    g = C.layered_u3_cz(n, 4, 2)
+    plan = Q.Plan(n, g)
+    got, st, _ = run_plan_on_gpu(n, plan)
+    ref = sim.apply(n, g)
+    assert abs(st.norm2() - np.sum(np.abs(got.astype(np.complex128)) ** 2)) < 1e-9
+    assert abs(st.norm2() - 1) < 1e-5
+    ref_dev = torch.from_numpy(ref.view(np.float64)).cuda()
+    fid, mx = st.compare_c128(ref_dev.data_ptr())
+    exp = abs(np.vdot(ref, got.astype(np.complex128))) ** 2 / np.sum(np.abs(got.astype(np.complex128)) ** 2)
+    assert abs(fid - exp) < 1e-12
+    assert abs(mx - np.max(np.abs(ref - got))) < 1e-7
+
+
+@pytest.mark.parametrize("n", [6, 14, 21])
+def test_remap_permutes_bits(n):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    rng = np.random.default_rng(n)
+    perm = rng.permutation(n)
+    x = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
+    src = torch.from_numpy(x.view(np.float32)).cuda()
+    dst = torch.empty_like(src)
+    Q.qs_remap(src.data_ptr(), dst.data_ptr(), n, perm, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    out = dst.cpu().numpy().view(np.complex64)
+    i = np.arange(1 << n)
+    j = np.zeros_like(i)
+    for b in range(n):
+        j |= ((i >> b) & 1) << int(perm[b])
+    ref = np.empty_like(x); ref[j] = x
+    assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5, 6, 7])
+def test_apply_fused_matches_kernel_unitary(k):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 16
+    rng = np.random.default_rng(k)
+    targets = [int(t) for t in rng.permutation(n)[:k]]
+    sub = C.mixed_circuit(k, 40, k) if k >= 2 else C.make_gates([(C.U3, 0, None, 0.4, 0.5, 0.6)])
+    u = sim.kernel_unitary(sub, list(range(k)))
+    # the same gates placed on `targets` of the n-qubit state
+    g = sub.copy()
+    g["q0"] = [targets[q] for q in sub["q0"]]
+    g["q1"] = [targets[q] if q >= 0 else -1 for q in sub["q1"]]
+    psi0 = sim.apply(n, C.hadamard_layer(n))
+    psi0 = sim.apply(n, C.mixed_circuit(n, 60, 3), psi0)
+    ref = sim.apply(n, g, psi0)
+    buf = torch.from_numpy(psi0.astype(np.complex64).view(np.float32)).cuda()
+    Q.qs_apply_fused(buf.data_ptr(), n, targets, u, Q.QS_PREC_FP32, torch.cuda.current_stream().cuda_stream)
+    got = buf.cpu().numpy().view(np.complex64)
+    assert_close_state(got, ref)
+
+
+def test_plan_fused_matrix_matches_oracle():
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 8
+    g = C.entangling_circuit(n, 2, 4)
+    cost = Q.default_cost_table()
+    for k in range(16):
+        cost.fuse_cost[k] = 1.0
+    plan = Q.Plan(n, g, algo=2, fuse_kmax=5, cost=cost)
+    found = 0
+    for k in range(plan.stats().num_kernels):
+        d = plan.kernel(k)
+        if d.type != Q.QS_KERNEL_FUSED:
+            continue
+        qubits = [q for q in range(n) if (d.qubit_mask >> q) & 1]
+        ids = plan.kernel_gates(k)
+        u_ref = sim.kernel_unitary(g[ids], qubits)
+        assert np.allclose(plan.fused_matrix(k), u_ref, atol=1e-12)
+        found += 1
+    assert found > 0
