@@ -198,10 +198,10 @@ def reference_arm(args):
     return 0
 
 
-def make_plan(Q, gates, which):
+def make_plan(Q, gates, which, shm_max=13):
     if which == "A":
         opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, cost_kind=Q.QS_COST_ANALYTIC,
-                              precision=Q.QS_PREC_FP32, shm_max_active=13, fuse_kmax=0)
+                              precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0)
         label = "A: analytic-cost OrderedKernelize, shared-memory kernels, FP32"
     else:
         raise ValueError(which)
@@ -217,6 +217,7 @@ def main():
     ap.add_argument("--plan", default="A")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--shm-max", type=int, default=13)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -236,7 +237,7 @@ def main():
     from synth import circuits as C
 
     gates = C.mixed_circuit(N_QUBITS, N_GATES, SEED)
-    plan, label = make_plan(Q, gates, args.plan)
+    plan, label = make_plan(Q, gates, args.plan, args.shm_max)
     ps = plan.stats()
     kdesc = [plan.kernel(k) for k in range(ps.num_kernels)]
     n = N_QUBITS
@@ -276,7 +277,8 @@ def main():
     pass_bytes = 16.0 * (1 << n)
     by_type = {}
     for k, d in enumerate(kdesc):
-        nm = "shm_kernel_v1" if d.type == Q.QS_KERNEL_SHM else "fused_fp32_kernel"
+        nm = ("shm_kernel_v2" if ps.num_phased else "shm_kernel_v1") if d.type == Q.QS_KERNEL_SHM \
+            else "fused_fp32_kernel"
         t = by_type.setdefault(nm, [0.0, 0])
         t[0] += per_kernel_ms[k]
         t[1] += runs

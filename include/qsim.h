@@ -105,6 +105,8 @@ typedef struct qs_plan_opts {
   int32_t prune_T;        /* Kernelize pruning threshold T (<= 0: no pruning)  */
   int32_t attach_single;  /* Kernelize: attach one-qubit gates to neighbours   */
   int32_t local_qubits;   /* L: qubits resident on the GPU per chunk (0 = n)   */
+  int32_t shm_variant;    /* shared-memory kernel: 0 auto, 1 generic tile kernel,
+                             2 register-phased kernel (tiles of 2^10..2^14)    */
   const qs_cost_table* cost; /* NULL: built-in table                           */
   const qs_mlp* mlp;         /* learned cost model (cost_kind = LEARNED)        */
 } qs_plan_opts;
@@ -135,6 +137,8 @@ typedef struct qs_plan_stats {
   double cost;        /* total model cost (Eq. 2)                           */
   double planner_ms;  /* host time spent in qs_plan_circuit                 */
   uint64_t dp_states; /* Kernelize: largest DP frontier                    */
+  uint64_t num_phased;    /* shm kernels run by the register-phased kernel   */
+  uint64_t num_exchanges; /* shared-memory exchanges summed over those       */
 } qs_plan_stats;
 int qs_plan_stats_get(const qs_plan* plan, qs_plan_stats* out);
 

@@ -45,7 +45,13 @@ static int ensure_device(PlanImpl* p, DeviceCache** out) {
       const auto& ops = p->shm[i].ops;
       host.resize(off + ops.size() * sizeof(DevOp));
       if (!ops.empty()) std::memcpy(host.data() + off, ops.data(), ops.size() * sizeof(DevOp));
+      const auto& pw = p->shm2[i].prog;
+      uint64_t poff = (host.size() + 255) & ~uint64_t(255);
+      host.resize(poff + pw.size() * sizeof(uint32_t));
+      if (!pw.empty()) std::memcpy(host.data() + poff, pw.data(), pw.size() * sizeof(uint32_t));
+      dc.prog_off.push_back(poff);
     } else {
+      dc.prog_off.push_back(0);
       const auto& u = p->fused[i].u;
       host.resize(off + u.size() * sizeof(float));
       std::memcpy(host.data() + off, u.data(), u.size() * sizeof(float));
@@ -121,6 +127,7 @@ void qs_plan_opts_default(qs_plan_opts* o) {
   o->prune_T = 500;
   o->attach_single = 1;
   o->local_qubits = 0;
+  o->shm_variant = 0;
   o->cost = nullptr;
   o->mlp = nullptr;
 }
@@ -140,6 +147,7 @@ int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_p
   if (o.algo < QS_ALGO_PER_GATE || o.algo > QS_ALGO_KERNELIZE) return QS_EINVAL;
   if (o.cost_kind == QS_COST_LEARNED && !o.mlp) return QS_EINVAL;
   if (o.cost_kind != QS_COST_ANALYTIC && o.cost_kind != QS_COST_LEARNED) return QS_EINVAL;
+  if (o.shm_variant < 0 || o.shm_variant > 2) return QS_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
   qs_plan* p = new (std::nothrow) qs_plan();
   if (!p) return QS_ENOMEM;
@@ -202,6 +210,11 @@ int qs_plan_stats_get(const qs_plan* p, qs_plan_stats* s) {
   s->cost = P.total_cost;
   s->planner_ms = P.planner_ms;
   s->dp_states = P.dp_states;
+  for (const auto& pg : P.shm2)
+    if (pg.ok) {
+      s->num_phased++;
+      s->num_exchanges += (uint64_t)(pg.num_phases - 1);
+    }
   return QS_OK;
 }
 
@@ -365,7 +378,15 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
       if (e != cudaSuccess) return cuda_status(e);
     }
     const uint8_t* base = static_cast<const uint8_t*>(dc->buf) + dc->op_off[i];
-    if (K.type == QS_KERNEL_SHM) {
+    if (K.type == QS_KERNEL_SHM && P->shm2[i].ok) {
+      ShmV2Launch a;
+      a.psi = st->psi;
+      a.n = P->n;
+      a.amask = K.mask;
+      a.prog = reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(dc->buf) + dc->prog_off[i]);
+      a.pg = &P->shm2[i];
+      rc = launch_shm_v2(a, s);
+    } else if (K.type == QS_KERNEL_SHM) {
       const ShmProgram& sp = P->shm[i];
       ShmLaunch a;
       a.psi = st->psi;

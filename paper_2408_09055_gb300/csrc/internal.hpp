@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "qsim.h"
+#include "shm_program.hpp"
 
 namespace qs {
 
@@ -73,6 +74,7 @@ struct DeviceCache {
   int device = -1;
   void* buf = nullptr;       // ops + matrices of every kernel
   std::vector<uint64_t> op_off;  // byte offset of kernel i's ops / matrix
+  std::vector<uint64_t> prog_off;  // byte offset of kernel i's phased program
 };
 
 struct PlanImpl {
@@ -83,6 +85,7 @@ struct PlanImpl {
   std::vector<Kernel> kernels;
   std::vector<ShmProgram> shm;      // indexed like kernels (empty for fused)
   std::vector<FusedProgram> fused;  // indexed like kernels (empty for shm)
+  std::vector<ShmProgramV2> shm2;   // register-phased programs (ok = false: generic kernel)
   double planner_ms = 0, total_cost = 0;
   uint64_t dp_states = 0;
   std::mutex mu;
@@ -109,6 +112,16 @@ struct ShmLaunch {
   int nops;
 };
 int launch_shm(const ShmLaunch& a, cudaStream_t s);
+
+struct ShmV2Launch {
+  float2* psi;
+  int n;
+  uint64_t amask;
+  const uint32_t* prog;      // device copy of pg->prog
+  const ShmProgramV2* pg;
+};
+int launch_shm_v2(const ShmV2Launch& a, cudaStream_t s);
+bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, ShmProgramV2* out);
 
 struct FusedLaunch {
   float2* psi;

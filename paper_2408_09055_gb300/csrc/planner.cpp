@@ -342,6 +342,7 @@ int compile_programs(PlanImpl* p) {
   const size_t K = p->kernels.size();
   p->shm.assign(K, ShmProgram());
   p->fused.assign(K, FusedProgram());
+  p->shm2.assign(K, ShmProgramV2());
   for (size_t i = 0; i < K; ++i) {
     Kernel& k = p->kernels[i];
     if (k.type == QS_KERNEL_SHM) {
@@ -349,6 +350,9 @@ int compile_programs(PlanImpl* p) {
       k.mask = widen_active(k.mask, p->n, want);
       if (std::popcount(k.mask) > kMaxShmActive) return QS_EPLAN;
       if (!compile_shm(p, k, &p->shm[i])) return QS_EPLAN;
+      if (p->opts.shm_variant != 1 && p->shm[i].m >= kMinPhasedM)
+        compile_shm_v2(p, k, p->shm[i], &p->shm2[i]);
+      if (p->opts.shm_variant == 2 && !p->shm2[i].ok) return QS_EUNSUPPORTED;
     } else {
       int want = std::min(p->n, std::max(p->opts.fuse_kmin, std::popcount(k.mask)));
       k.mask = widen_fused(k.mask, p->n, want);

@@ -49,6 +49,7 @@ class qs_plan_opts(ctypes.Structure):
                 ("forced_low", ctypes.c_int32), ("fuse_kmin", ctypes.c_int32),
                 ("fuse_kmax", ctypes.c_int32), ("prune_T", ctypes.c_int32),
                 ("attach_single", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
+                ("shm_variant", ctypes.c_int32),
                 ("cost", ctypes.POINTER(qs_cost_table)), ("mlp", ctypes.c_void_p)]
 
 
@@ -57,7 +58,8 @@ class qs_plan_stats(ctypes.Structure):
                 ("num_gates", ctypes.c_uint64), ("num_kernels", ctypes.c_uint64),
                 ("num_shm", ctypes.c_uint64), ("num_fused", ctypes.c_uint64),
                 ("cost", ctypes.c_double), ("planner_ms", ctypes.c_double),
-                ("dp_states", ctypes.c_uint64)]
+                ("dp_states", ctypes.c_uint64), ("num_phased", ctypes.c_uint64),
+                ("num_exchanges", ctypes.c_uint64)]
 
 
 class qs_kernel_desc(ctypes.Structure):
