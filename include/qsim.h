@@ -105,8 +105,11 @@ typedef struct qs_plan_opts {
   int32_t prune_T;        /* Kernelize pruning threshold T (<= 0: no pruning)  */
   int32_t attach_single;  /* Kernelize: attach one-qubit gates to neighbours   */
   int32_t local_qubits;   /* L: qubits resident on the GPU per chunk (0 = n)   */
-  int32_t shm_variant;    /* shared-memory kernel: 0 auto, 1 generic tile kernel,
-                             2 register-phased kernel (tiles of 2^10..2^14)    */
+  int32_t shm_variant;    /* shared-memory kernel: 0 auto (specialised if it
+                             compiles, else interpreted, else generic),
+                             1 generic tile kernel, 2 register-phased
+                             interpreter, 3 register-phased kernel specialised
+                             per plan (NVRTC, sm_103a)                         */
   const qs_cost_table* cost; /* NULL: built-in table                           */
   const qs_mlp* mlp;         /* learned cost model (cost_kind = LEARNED)        */
 } qs_plan_opts;
@@ -139,6 +142,8 @@ typedef struct qs_plan_stats {
   uint64_t dp_states; /* Kernelize: largest DP frontier                    */
   uint64_t num_phased;    /* shm kernels run by the register-phased kernel   */
   uint64_t num_exchanges; /* shared-memory exchanges summed over those       */
+  uint64_t num_jit;       /* of those, kernels specialised per plan (NVRTC)  */
+  double jit_ms;          /* host time compiling them (included in planner_ms) */
 } qs_plan_stats;
 int qs_plan_stats_get(const qs_plan* plan, qs_plan_stats* out);
 
@@ -157,6 +162,11 @@ int64_t qs_plan_kernel_gates(const qs_plan* plan, uint64_t k, int32_t* ids, uint
 /* The fused kernel's unitary in FP64, row-major complex interleaved,
  * 2^k x 2^k, index bit j = the j-th lowest qubit of qubit_mask.            */
 int qs_plan_fused_matrix(const qs_plan* plan, uint64_t k, double* out, uint64_t cap_doubles);
+/* The CUDA source of shared-memory kernel k specialised for this plan (the
+ * text compiled with NVRTC), NUL-terminated into out[0..cap); returns its
+ * length (excluding the NUL), or a negative status (QS_EINVAL when kernel k
+ * has no specialised form).  With out == NULL only the length is returned. */
+int64_t qs_plan_kernel_source(const qs_plan* plan, uint64_t k, char* out, uint64_t cap);
 /* Checks Theorem 2 on a plan: every gate exactly once and, for every pair of
  * gates sharing a qubit that is not insular in both, circuit order kept.
  * QS_OK or QS_EPLAN.                                                        */

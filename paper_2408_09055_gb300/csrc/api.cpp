@@ -57,6 +57,39 @@ static int ensure_device(PlanImpl* p, DeviceCache** out) {
       std::memcpy(host.data() + off, u.data(), u.size() * sizeof(float));
     }
   }
+  // specialised kernels: load the JIT modules and look up each kernel
+  dc.jit_kernel.assign(p->kernels.size(), nullptr);
+  for (size_t k = 0; k < p->jit_modules.size(); ++k) {
+    cudaLibrary_t lib = nullptr;
+    if (!p->jit_modules[k].empty()) {
+      e = cudaLibraryLoadData(&lib, p->jit_modules[k].data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+      if (e != cudaSuccess) {
+        for (auto l : dc.libs) cudaLibraryUnload(l);
+        return cuda_status(e);
+      }
+    }
+    dc.libs.push_back(lib);
+  }
+  for (size_t i = 0; i < p->kernels.size(); ++i) {
+    const int mod = (i < p->shm2.size() && p->shm2[i].ok) ? p->shm2[i].jit_module : -1;
+    if (mod < 0 || !dc.libs[mod]) continue;
+    std::string name = "qsk" + std::to_string(i);
+    cudaKernel_t kf = nullptr;
+    e = cudaLibraryGetKernel(&kf, dc.libs[mod], name.c_str());
+    if (e != cudaSuccess) {
+      for (auto l : dc.libs)
+        if (l) cudaLibraryUnload(l);
+      return cuda_status(e);
+    }
+    const int smem = (int)(sizeof(float2) * pad_size(p->shm2[i].m));
+    e = cudaKernelSetAttributeForDevice(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem, dev);
+    if (e != cudaSuccess) {
+      for (auto l : dc.libs)
+        if (l) cudaLibraryUnload(l);
+      return cuda_status(e);
+    }
+    dc.jit_kernel[i] = kf;
+  }
   if (host.empty()) host.resize(256);
   e = cudaMalloc(&dc.buf, host.size());
   if (e != cudaSuccess) return cuda_status(e);
@@ -147,7 +180,7 @@ int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_p
   if (o.algo < QS_ALGO_PER_GATE || o.algo > QS_ALGO_KERNELIZE) return QS_EINVAL;
   if (o.cost_kind == QS_COST_LEARNED && !o.mlp) return QS_EINVAL;
   if (o.cost_kind != QS_COST_ANALYTIC && o.cost_kind != QS_COST_LEARNED) return QS_EINVAL;
-  if (o.shm_variant < 0 || o.shm_variant > 2) return QS_EINVAL;
+  if (o.shm_variant < 0 || o.shm_variant > 3) return QS_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
   qs_plan* p = new (std::nothrow) qs_plan();
   if (!p) return QS_ENOMEM;
@@ -189,10 +222,10 @@ void qs_plan_free(qs_plan* p) {
   int cur = -1;
   cudaGetDevice(&cur);
   for (auto& d : p->impl.dev) {
-    if (d.buf) {
-      cudaSetDevice(d.device);
-      cudaFree(d.buf);
-    }
+    cudaSetDevice(d.device);
+    if (d.buf) cudaFree(d.buf);
+    for (auto l : d.libs)
+      if (l) cudaLibraryUnload(l);
   }
   if (cur >= 0 && !p->impl.dev.empty()) cudaSetDevice(cur);
   delete p;
@@ -214,7 +247,9 @@ int qs_plan_stats_get(const qs_plan* p, qs_plan_stats* s) {
     if (pg.ok) {
       s->num_phased++;
       s->num_exchanges += (uint64_t)(pg.num_phases - 1);
+      if (pg.jit_module >= 0) s->num_jit++;
     }
+  s->jit_ms = P.jit_ms;
   return QS_OK;
 }
 
@@ -247,6 +282,18 @@ int qs_plan_fused_matrix(const qs_plan* p, uint64_t k, double* out, uint64_t cap
   if (cap < u.size()) return QS_EINVAL;
   std::copy(u.begin(), u.end(), out);
   return QS_OK;
+}
+
+int64_t qs_plan_kernel_source(const qs_plan* p, uint64_t k, char* out, uint64_t cap) {
+  if (!p || k >= p->impl.kernels.size()) return QS_EINVAL;
+  if (k >= p->impl.shm2.size() || !p->impl.shm2[k].ok) return QS_EINVAL;
+  std::string src;
+  if (!jit_source(p->impl.shm2[k], p->impl.n, "qsk" + std::to_string(k), &src)) return QS_EINVAL;
+  if (out) {
+    if (cap < src.size() + 1) return QS_EINVAL;
+    std::memcpy(out, src.c_str(), src.size() + 1);
+  }
+  return (int64_t)src.size();
 }
 
 int qs_plan_validate(const qs_plan* p, const qs_gate* gates, uint64_t ngates) {
@@ -378,7 +425,9 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
       if (e != cudaSuccess) return cuda_status(e);
     }
     const uint8_t* base = static_cast<const uint8_t*>(dc->buf) + dc->op_off[i];
-    if (K.type == QS_KERNEL_SHM && P->shm2[i].ok) {
+    if (K.type == QS_KERNEL_SHM && dc->jit_kernel[i]) {
+      rc = launch_jit(dc->jit_kernel[i], P->shm2[i], st->psi, P->n, s);
+    } else if (K.type == QS_KERNEL_SHM && P->shm2[i].ok) {
       ShmV2Launch a;
       a.psi = st->psi;
       a.n = P->n;

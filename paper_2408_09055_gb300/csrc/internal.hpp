@@ -75,6 +75,8 @@ struct DeviceCache {
   void* buf = nullptr;       // ops + matrices of every kernel
   std::vector<uint64_t> op_off;  // byte offset of kernel i's ops / matrix
   std::vector<uint64_t> prog_off;  // byte offset of kernel i's phased program
+  std::vector<cudaLibrary_t> libs;     // loaded JIT modules
+  std::vector<cudaKernel_t> jit_kernel;  // per plan kernel (nullptr: none)
 };
 
 struct PlanImpl {
@@ -86,6 +88,9 @@ struct PlanImpl {
   std::vector<ShmProgram> shm;      // indexed like kernels (empty for fused)
   std::vector<FusedProgram> fused;  // indexed like kernels (empty for shm)
   std::vector<ShmProgramV2> shm2;   // register-phased programs (ok = false: generic kernel)
+  std::vector<std::vector<char>> jit_modules;  // cubins of the specialised kernels
+  std::string jit_log;              // first NVRTC error log, if any
+  double jit_ms = 0;
   double planner_ms = 0, total_cost = 0;
   uint64_t dp_states = 0;
   std::mutex mu;
@@ -122,6 +127,10 @@ struct ShmV2Launch {
 };
 int launch_shm_v2(const ShmV2Launch& a, cudaStream_t s);
 bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, ShmProgramV2* out);
+void fold_global_phase(std::vector<ShmProgramV2>& progs);
+int jit_compile_plan(PlanImpl* p);                 // jit.cpp
+bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::string* out);
+int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, cudaStream_t s);
 
 struct FusedLaunch {
   float2* psi;

@@ -1,0 +1,488 @@
+// Plan-time specialisation of shared-memory kernels (kernel type 2 of the
+// paper's "Cost Function in Kernelize"; insular handling of Appendix A.2).
+//
+// Each register-phased program (shm_program.cpp) is turned into one
+// straight-line CUDA kernel and compiled for sm_103a with NVRTC:
+//  * every register bit, thread bit, matrix entry and HBM/shared-memory
+//    offset is a compile-time constant, so the interpreter's dispatch,
+//    control masks and runtime address arithmetic disappear;
+//  * X, CX on register bits and SWAP become register renames (no code);
+//  * zero and unit terms of every 2x2 and diagonal factor are dropped;
+//  * the exchange tile uses the padded layout pad_index(), which is
+//    additive, so each shared access is `tile[thread_offset + constant]`.
+// Kernels are compiled in parallel batches; the cubins are cached on disk
+// keyed by a hash of the source.
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cinttypes>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
+#include <sys/stat.h>
+#include <thread>
+
+#include "internal.hpp"
+#include "shm_program.hpp"
+
+namespace qs {
+
+namespace {
+
+std::string flit(float v) {
+  char b[48];
+  std::snprintf(b, sizeof b, "%.9ef", (double)v);
+  return b;
+}
+
+float word_f(uint32_t w) {
+  float f;
+  std::memcpy(&f, &w, 4);
+  return f;
+}
+
+// One real component of a sum of products: terms (coef, operand).
+std::string lin(const std::vector<std::pair<float, std::string>>& terms) {
+  std::string acc;
+  for (const auto& t : terms) {
+    float c = t.first;
+    if (c == 0.0f) continue;
+    if (acc.empty()) {
+      if (c == 1.0f) acc = t.second;
+      else if (c == -1.0f) acc = "(-" + t.second + ")";
+      else acc = "(" + flit(c) + "*" + t.second + ")";
+    } else {
+      if (c == 1.0f) acc = "(" + acc + "+" + t.second + ")";
+      else if (c == -1.0f) acc = "(" + acc + "-" + t.second + ")";
+      else acc = "fmaf(" + flit(c) + "," + t.second + "," + acc + ")";
+    }
+  }
+  return acc.empty() ? std::string("0.0f") : acc;
+}
+
+struct CF {
+  float re, im;
+};
+
+// re/im parts of sum_c u_c * v_c for complex constants u_c and variables v_c
+std::string cre(const std::vector<std::pair<CF, std::string>>& t) {
+  std::vector<std::pair<float, std::string>> r;
+  for (auto& x : t) {
+    r.push_back({x.first.re, x.second + ".x"});
+    r.push_back({-x.first.im, x.second + ".y"});
+  }
+  return lin(r);
+}
+std::string cim(const std::vector<std::pair<CF, std::string>>& t) {
+  std::vector<std::pair<float, std::string>> r;
+  for (auto& x : t) {
+    r.push_back({x.first.re, x.second + ".y"});
+    r.push_back({x.first.im, x.second + ".x"});
+  }
+  return lin(r);
+}
+
+bool unit(CF c) { return c.re == 1.0f && c.im == 0.0f; }
+
+struct Gen {
+  const ShmProgramV2& pg;
+  std::ostringstream o;
+  int nm[kRegAmps];  // register index j -> variable r<nm[j]>
+  int phase = 0;
+  explicit Gen(const ShmProgramV2& p) : pg(p) {
+    for (int j = 0; j < kRegAmps; ++j) nm[j] = j;
+  }
+  std::string v(int j) const { return "r" + std::to_string(nm[j]); }
+
+  // value (0/1) of a qubit reference that is not a register slot
+  std::string known(uint32_t ref) const {
+    if (ref & REF_GLOBAL) return "((unsigned)(base >> " + std::to_string(ref & 63u) + ") & 1u)";
+    const PhaseMap& pm = pg.maps[phase];
+    int b = (int)(ref & 31u);
+    for (int k = 0; k < pm.nt; ++k)
+      if (pm.T[k] == b) return "((tid >> " + std::to_string(k) + ") & 1u)";
+    return "0u";  // unreachable for a well-formed program
+  }
+
+  void mulc(int j, CF e) {  // r_j *= e
+    if (unit(e)) return;
+    std::string x = v(j);
+    o << "{const float2 x=" << x << ";" << x << "=make_float2(" << cre({{e, "x"}}) << ","
+      << cim({{e, "x"}}) << ");}\n";
+  }
+
+  void g1(int t, CF u00, CF u01, CF u10, CF u11) {
+    for (int j = 0; j < kRegAmps; ++j) {
+      if (j & (1 << t)) continue;
+      int k = j | (1 << t);
+      std::string a = v(j), b = v(k);
+      o << "{const float2 x=" << a << ",y=" << b << ";" << a << "=make_float2("
+        << cre({{u00, "x"}, {u01, "y"}}) << "," << cim({{u00, "x"}, {u01, "y"}}) << ");" << b
+        << "=make_float2(" << cre({{u10, "x"}, {u11, "y"}}) << "," << cim({{u10, "x"}, {u11, "y"}})
+        << ");}\n";
+    }
+  }
+
+  void swap_pair(int j, int k) { std::swap(nm[j], nm[k]); }
+
+  void xchg(const PhaseMap& next, int next_index) {
+    o << "__syncthreads();\n";
+    const PhaseMap& cur = pg.maps[phase];
+    for (int j = 0; j < kRegAmps; ++j) {
+      uint32_t li = 0;
+      for (int i = 0; i < kRegBits; ++i)
+        if ((j >> i) & 1) li |= 1u << cur.R[i];
+      o << "tile[sp" << phase << "+" << pad_index(li) << "u]=" << v(j) << ";\n";
+    }
+    o << "__syncthreads();\n";
+    for (int j = 0; j < kRegAmps; ++j) {
+      nm[j] = j;
+      uint32_t li = 0;
+      for (int i = 0; i < kRegBits; ++i)
+        if ((j >> i) & 1) li |= 1u << next.R[i];
+      o << v(j) << "=tile[sp" << next_index << "+" << pad_index(li) << "u];\n";
+    }
+    phase = next_index;
+  }
+
+  bool body() {
+    const std::vector<uint32_t>& w = pg.prog;
+    size_t pc = 0;
+    int xchg_seen = 0;
+    auto cf = [&](size_t at) { return CF{word_f(w[at]), word_f(w[at + 1])}; };
+    while (pc < w.size()) {
+      const uint32_t op = w[pc] & 0xFFu, A = (w[pc] >> 8) & 0xFFu, B = (w[pc] >> 16) & 0xFFu,
+                     Cu = w[pc] >> 24;
+      switch (op) {
+        case PK_END:
+          return true;
+        case PK_G1:
+          g1((int)A, cf(pc + 1), cf(pc + 3), cf(pc + 5), cf(pc + 7));
+          pc += 9;
+          break;
+        case PK_G1R:
+          g1((int)A, CF{word_f(w[pc + 1]), 0}, CF{word_f(w[pc + 2]), 0}, CF{word_f(w[pc + 3]), 0},
+             CF{word_f(w[pc + 4]), 0});
+          pc += 5;
+          break;
+        case PK_G1X:
+          g1((int)A, CF{word_f(w[pc + 1]), 0}, CF{0, word_f(w[pc + 2])}, CF{0, word_f(w[pc + 3])},
+             CF{word_f(w[pc + 4]), 0});
+          pc += 5;
+          break;
+        case PK_G1C: {
+          CF u00 = cf(pc + 1), u01 = cf(pc + 3), u10 = cf(pc + 5), u11 = cf(pc + 7);
+          if (B < (uint32_t)kRegBits) {
+            for (int j = 0; j < kRegAmps; ++j) {
+              if ((j & (1 << A)) || !((j >> B) & 1)) continue;
+              int k = j | (1 << A);
+              std::string a = v(j), b = v(k);
+              o << "{const float2 x=" << a << ",y=" << b << ";" << a << "=make_float2("
+                << cre({{u00, "x"}, {u01, "y"}}) << "," << cim({{u00, "x"}, {u01, "y"}}) << ");"
+                << b << "=make_float2(" << cre({{u10, "x"}, {u11, "y"}}) << ","
+                << cim({{u10, "x"}, {u11, "y"}}) << ");}\n";
+            }
+          } else {
+            o << "if (" << known(B) << ") {\n";
+            g1((int)A, u00, u01, u10, u11);
+            o << "}\n";
+          }
+          pc += 9;
+          break;
+        }
+        case PK_XG:
+          for (int j = 0; j < kRegAmps; ++j)
+            if (!(j & (1 << A))) swap_pair(j, j | (1 << A));
+          pc += 1;
+          break;
+        case PK_XGS:
+          for (int j = 0; j < kRegAmps; ++j)
+            if (!(j & (1 << A)) && ((j >> B) & 1)) swap_pair(j, j | (1 << A));
+          pc += 1;
+          break;
+        case PK_XGK:
+          o << "if (" << known(B) << ") {\n";
+          for (int j = 0; j < kRegAmps; ++j)
+            if (!(j & (1 << A))) {
+              std::string a = v(j), b = v(j | (1 << A));
+              o << "{const float2 x=" << a << ";" << a << "=" << b << ";" << b << "=x;}\n";
+            }
+          o << "}\n";
+          pc += 1;
+          break;
+        case PK_D1B: {
+          CF e = cf(pc + 1);
+          for (int j = 0; j < kRegAmps; ++j)
+            if (j & (1 << A)) mulc(j, e);
+          pc += 3;
+          break;
+        }
+        case PK_D1: {
+          CF e0 = cf(pc + 1), e1 = cf(pc + 3);
+          for (int j = 0; j < kRegAmps; ++j) mulc(j, (j & (1 << A)) ? e1 : e0);
+          pc += 5;
+          break;
+        }
+        case PK_D1K: {
+          CF d[4] = {cf(pc + 1), cf(pc + 3), cf(pc + 5), cf(pc + 7)};
+          for (int kb = 0; kb < 2; ++kb) {
+            if (unit(d[2 * kb]) && unit(d[2 * kb + 1])) continue;
+            o << "if (" << known(B) << (kb ? "" : " == 0u") << ") {\n";
+            for (int j = 0; j < kRegAmps; ++j) mulc(j, d[2 * kb + ((j >> A) & 1)]);
+            o << "}\n";
+          }
+          pc += 9;
+          break;
+        }
+        case PK_D2: {
+          CF d[4] = {cf(pc + 1), cf(pc + 3), cf(pc + 5), cf(pc + 7)};
+          for (int j = 0; j < kRegAmps; ++j) mulc(j, d[((j >> A) & 1) | (((j >> B) & 1) << 1)]);
+          pc += 9;
+          break;
+        }
+        case PK_D2P: {
+          CF e = cf(pc + 1);
+          for (int j = 0; j < kRegAmps; ++j)
+            if (((j >> A) & 1) && ((j >> B) & 1)) mulc(j, e);
+          pc += 3;
+          break;
+        }
+        case PK_D0: {
+          CF d[4] = {cf(pc + 1), cf(pc + 3), cf(pc + 5), cf(pc + 7)};
+          std::string k0 = known(A), k1 = (B == REF_NONE) ? std::string("0u") : known(B);
+          for (int idx = 0; idx < 4; ++idx) {
+            if ((Cu >> idx) & 1u) continue;
+            if (B == REF_NONE && idx >= 2) continue;
+            o << "if (" << k0 << " == " << (idx & 1) << "u && " << k1 << " == " << (idx >> 1)
+              << "u) {\n";
+            for (int j = 0; j < kRegAmps; ++j) mulc(j, d[idx]);
+            o << "}\n";
+          }
+          pc += 9;
+          break;
+        }
+        case PK_SWAPR:
+          for (int j = 0; j < kRegAmps; ++j)
+            if (((j >> A) & 1) && !((j >> B) & 1)) swap_pair(j, j ^ (1 << A) ^ (1 << B));
+          pc += 1;
+          break;
+        case PK_XX: {
+          float c = word_f(w[pc + 1]), s = word_f(w[pc + 2]);
+          for (int j = 0; j < kRegAmps; ++j) {
+            if ((j >> B) & 1) continue;
+            int k = j ^ (1 << A) ^ (1 << B);
+            CF cc{c, 0}, ms{0, -s};
+            std::string a = v(j), b = v(k);
+            o << "{const float2 x=" << a << ",y=" << b << ";" << a << "=make_float2("
+              << cre({{cc, "x"}, {ms, "y"}}) << "," << cim({{cc, "x"}, {ms, "y"}}) << ");" << b
+              << "=make_float2(" << cre({{ms, "x"}, {cc, "y"}}) << "," << cim({{ms, "x"}, {cc, "y"}})
+              << ");}\n";
+          }
+          pc += 3;
+          break;
+        }
+        case PK_SCALE: {
+          CF e = cf(pc + 1);
+          for (int j = 0; j < kRegAmps; ++j) mulc(j, e);
+          pc += 3;
+          break;
+        }
+        case PK_XCHG:
+          ++xchg_seen;
+          if (xchg_seen >= (int)pg.maps.size()) return false;
+          xchg(pg.maps[xchg_seen], xchg_seen);
+          pc += 1 + kRegBits + A;
+          break;
+        default:
+          return false;
+      }
+    }
+    return false;
+  }
+};
+
+std::string thread_expr(const PhaseMap& pm, const uint64_t* value_of_local) {
+  std::ostringstream e;
+  e << "0u";
+  for (int k = 0; k < pm.nt; ++k) {
+    uint64_t val = value_of_local[pm.T[k]];
+    e << " + (((tid >> " << k << ") & 1u) * " << val << "u)";
+  }
+  return e.str();
+}
+
+}  // namespace
+
+bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::string* out) {
+  const int m = pg.m;
+  const int nt = m - kRegBits;
+  Gen g(pg);
+  std::ostringstream& o = g.o;
+  uint64_t phys[kMaxShmActive], padv[kMaxShmActive];
+  for (int j = 0; j < m; ++j) {
+    phys[j] = 1ull << pg.act[j];
+    padv[j] = pad_index(1u << j);
+    if (pg.act[j] >= 32) return false;
+  }
+  const int minb = 1 << (kMaxShmActive - m);
+  o << "extern \"C\" __global__ void __launch_bounds__(" << (1 << nt) << ", " << minb << ")\n"
+    << name << "(float2* __restrict__ psi, unsigned long long nb) {\n"
+    << "extern __shared__ float2 tile[];\n"
+    << "const unsigned tid = threadIdx.x;\n";
+  o << "const unsigned ptl = " << thread_expr(pg.maps.front(), phys) << ";\n";
+  o << "const unsigned pts = " << thread_expr(pg.maps.back(), phys) << ";\n";
+  for (size_t p = 0; p < pg.maps.size(); ++p)
+    o << "const unsigned sp" << p << " = " << thread_expr(pg.maps[p], padv) << ";\n";
+  o << "for (unsigned long long bt = blockIdx.x; bt < nb; bt += gridDim.x) {\n";
+  o << "const unsigned long long base = 0ull";
+  for (int r = 0; r < pg.nruns; ++r)
+    o << " | (((bt >> " << (int)pg.run_src[r] << ") & " << ((1ull << pg.run_len[r]) - 1) << "ull) << "
+      << (int)pg.run_dst[r] << ")";
+  o << ";\n";
+  o << "const float2* __restrict__ ip = psi + (base | ptl);\n";
+  {
+    const PhaseMap& lm = pg.maps.front();
+    for (int j = 0; j < kRegAmps; ++j) {
+      uint64_t off = 0;
+      for (int i = 0; i < kRegBits; ++i)
+        if ((j >> i) & 1) off |= phys[lm.R[i]];
+      o << "float2 r" << j << " = ip[" << off << "u];\n";
+    }
+  }
+  if (!g.body()) return false;
+  if (g.phase != (int)pg.maps.size() - 1) return false;
+  o << "float2* __restrict__ op = psi + (base | pts);\n";
+  {
+    const PhaseMap& sm = pg.maps.back();
+    for (int j = 0; j < kRegAmps; ++j) {
+      uint64_t off = 0;
+      for (int i = 0; i < kRegBits; ++i)
+        if ((j >> i) & 1) off |= phys[sm.R[i]];
+      o << "op[" << off << "u] = " << g.v(j) << ";\n";
+    }
+  }
+  o << "}\n}\n";
+  (void)n;
+  *out = o.str();
+  return true;
+}
+
+// ---- NVRTC -----------------------------------------------------------------------
+
+static uint64_t fnv1a(const std::string& s) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char c : s) {
+    h ^= c;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+static std::string cache_dir() {
+  const char* e = std::getenv("QSIM_JIT_CACHE");
+  if (e && *e) return e;
+  const char* home = std::getenv("HOME");
+  std::string d = std::string(home && *home ? home : "/tmp") + "/.cache/qsim-jit";
+  return d;
+}
+
+static void mkdirs(const std::string& d) {
+  std::string cur;
+  for (size_t i = 0; i < d.size(); ++i) {
+    cur += d[i];
+    if (d[i] == '/' && cur.size() > 1) mkdir(cur.c_str(), 0755);
+  }
+  mkdir(d.c_str(), 0755);
+}
+
+static bool compile_one(const std::string& src, std::vector<char>* cubin, std::string* log) {
+  const std::string dir = cache_dir();
+  char key[32];
+  std::snprintf(key, sizeof key, "%016" PRIx64, fnv1a(src));
+  const std::string path = dir + "/" + key + ".cubin";
+  {
+    std::ifstream f(path, std::ios::binary);
+    if (f) {
+      cubin->assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+      if (!cubin->empty()) return true;
+    }
+  }
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "qsim_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+    return false;
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+  nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  if (r != NVRTC_SUCCESS) {
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    log->resize(ls);
+    nvrtcGetProgramLog(prog, log->data());
+    nvrtcDestroyProgram(&prog);
+    return false;
+  }
+  size_t sz = 0;
+  nvrtcGetCUBINSize(prog, &sz);
+  cubin->resize(sz);
+  nvrtcGetCUBIN(prog, cubin->data());
+  nvrtcDestroyProgram(&prog);
+  mkdirs(dir);
+  const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)std::hash<std::thread::id>{}(std::this_thread::get_id()));
+  {
+    std::ofstream f(tmp, std::ios::binary);
+    f.write(cubin->data(), (std::streamsize)cubin->size());
+  }
+  std::rename(tmp.c_str(), path.c_str());
+  return true;
+}
+
+// Compiles every phased program of the plan into cubins (one module per
+// batch of kernels), in parallel.  Programs that fail keep the interpreter.
+int jit_compile_plan(PlanImpl* p) {
+  std::vector<int> idx;
+  for (size_t i = 0; i < p->shm2.size(); ++i)
+    if (p->shm2[i].ok) idx.push_back((int)i);
+  p->jit_modules.clear();
+  if (idx.empty()) return QS_OK;
+  const int per_module = 8;
+  const int nmod = (int)((idx.size() + per_module - 1) / per_module);
+  std::vector<std::string> srcs(nmod);
+  std::vector<std::vector<int>> members(nmod);
+  for (size_t t = 0; t < idx.size(); ++t) {
+    int i = idx[t];
+    std::string name = "qsk" + std::to_string(i), s;
+    if (!jit_source(p->shm2[i], p->n, name, &s)) continue;
+    srcs[t / per_module] += s;
+    members[t / per_module].push_back(i);
+  }
+  p->jit_modules.assign(nmod, std::vector<char>());
+  std::vector<char> ok(nmod, 0);
+  std::atomic<int> next{0};
+  std::string first_log;
+  std::mutex log_mu;
+  unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  unsigned nth = std::min<unsigned>(hw, (unsigned)nmod);
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nth; ++t)
+    th.emplace_back([&]() {
+      for (int k; (k = next.fetch_add(1)) < nmod;) {
+        if (srcs[k].empty()) continue;
+        std::string log;
+        ok[k] = compile_one(srcs[k], &p->jit_modules[k], &log);
+        if (!ok[k]) {
+          std::lock_guard<std::mutex> lk(log_mu);
+          if (first_log.empty()) first_log = log;
+        }
+      }
+    });
+  for (auto& t : th) t.join();
+  for (int k = 0; k < nmod; ++k)
+    for (int i : members[k]) {
+      p->shm2[i].jit_module = ok[k] ? k : -1;
+    }
+  p->jit_log = first_log;
+  return QS_OK;
+}
+
+}  // namespace qs

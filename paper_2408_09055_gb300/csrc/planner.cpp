@@ -352,13 +352,23 @@ int compile_programs(PlanImpl* p) {
       if (!compile_shm(p, k, &p->shm[i])) return QS_EPLAN;
       if (p->opts.shm_variant != 1 && p->shm[i].m >= kMinPhasedM)
         compile_shm_v2(p, k, p->shm[i], &p->shm2[i]);
-      if (p->opts.shm_variant == 2 && !p->shm2[i].ok) return QS_EUNSUPPORTED;
+      if (p->opts.shm_variant >= 2 && !p->shm2[i].ok) return QS_EUNSUPPORTED;
     } else {
       int want = std::min(p->n, std::max(p->opts.fuse_kmin, std::popcount(k.mask)));
       k.mask = widen_fused(k.mask, p->n, want);
       if (std::popcount(k.mask) > kMaxFuse) return QS_EPLAN;
       compile_fused(p, k, &p->fused[i]);
     }
+  }
+  fold_global_phase(p->shm2);
+  if (p->opts.shm_variant == 0 || p->opts.shm_variant == 3) {
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = jit_compile_plan(p);
+    p->jit_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc != QS_OK) return rc;
+    if (p->opts.shm_variant == 3)
+      for (const auto& pg : p->shm2)
+        if (pg.ok && pg.jit_module < 0) return QS_EUNSUPPORTED;
   }
   return QS_OK;
 }

@@ -31,13 +31,21 @@ namespace {
 
 using cd = std::complex<double>;
 
+// One op before serialisation.  kind PK_G1 with single_slot set is a raw
+// uncontrolled one-slot matrix, classified into its cheapest form when the
+// program is written out.
 struct HostOp {
   uint32_t kind = PK_END, a = 0, b = REF_NONE, c = 0;
-  cd m[4];                 // G1 matrix (row-major) or D* diagonal entries
+  cd m[4];                 // 2x2 matrix (row-major) or diagonal entries d[4]
   double x0 = 0, x1 = 0;   // XX: cos, sin
-  bool single_slot = false;  // uncontrolled one-slot op (mergeable)
+  bool single_slot = false;  // uncontrolled one-slot matrix (mergeable)
   PhaseMap map;            // XCHG target map
 };
+
+bool is_one(cd v) { return (float)v.real() == 1.0f && (float)v.imag() == 0.0f; }
+bool is_zero(cd v) { return (float)v.real() == 0.0f && (float)v.imag() == 0.0f; }
+bool is_real(cd v) { return (float)v.imag() == 0.0f; }
+bool is_imag(cd v) { return (float)v.real() == 0.0f; }
 
 void assign_threads(PhaseMap& pm, int m) {
   uint32_t rmask = 0;
@@ -95,17 +103,6 @@ uint32_t unit_mask(const cd* d) {
   return u;
 }
 
-void push_floats(std::vector<uint32_t>& w, const cd* v, int n) {
-  for (int i = 0; i < n; ++i) {
-    float re = (float)v[i].real(), im = (float)v[i].imag();
-    uint32_t a, b;
-    std::memcpy(&a, &re, 4);
-    std::memcpy(&b, &im, 4);
-    w.push_back(a);
-    w.push_back(b);
-  }
-}
-
 }  // namespace
 
 bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, ShmProgramV2* out) {
@@ -113,10 +110,36 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
   out->ok = false;
   out->prog.clear();
   if (m < kMinPhasedM || m > kMaxShmActive) return false;
+  for (int j = 0; j < m; ++j)
+    if (sp.act[j] >= 32) return false;  // 32-bit amplitude offsets inside a batch
   out->m = m;
   int loc[kMaxQubits];
   for (int q = 0; q < kMaxQubits; ++q) loc[q] = -1;
-  for (int j = 0; j < m; ++j) loc[sp.act[j]] = j;
+  uint64_t amask = 0;
+  for (int j = 0; j < m; ++j) {
+    loc[sp.act[j]] = j;
+    amask |= 1ull << sp.act[j];
+  }
+  // runs of non-active physical bits, for the batch-index deposit
+  out->nruns = 0;
+  {
+    int src = 0;
+    for (int q = 0; q < p->n;) {
+      if ((amask >> q) & 1) {
+        ++q;
+        continue;
+      }
+      int len = 0;
+      while (q + len < p->n && !((amask >> (q + len)) & 1)) ++len;
+      if (out->nruns >= 16) return false;
+      out->run_src[out->nruns] = (uint8_t)src;
+      out->run_len[out->nruns] = (uint8_t)len;
+      out->run_dst[out->nruns] = (uint8_t)q;
+      out->nruns++;
+      src += len;
+      q += len;
+    }
+  }
 
   const size_t G = K.gates.size();
   std::vector<const Gate*> gs(G);
@@ -146,6 +169,7 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
   const uint32_t low4 = 0xF;
 
   std::vector<HostOp> ops;
+  cd gphase = 1.0;
   // initial (load) phase: register bits avoid the low local bits
   uint32_t r = 0;
   for (size_t i = 0; i < G; ++i)
@@ -153,6 +177,9 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
   r = fill_regs(r, tmask, done, m, low4);
   PhaseMap cur = make_map(r, m);
   out->load = cur;
+  out->maps.clear();
+  out->maps.push_back(cur);
+  for (int j = 0; j < m; ++j) out->act[j] = sp.act[j];
   int slot_of[kMaxShmActive];
   auto set_slots = [&](const PhaseMap& pm) {
     for (int b = 0; b < m; ++b) slot_of[b] = -1;
@@ -167,7 +194,21 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
   };
   auto is_slot = [](uint32_t rf) { return rf < (uint32_t)kRegBits; };
 
-  auto emit = [&](const Gate& g) {
+  auto push = [&](HostOp op) {
+    // merge consecutive uncontrolled one-slot matrices on the same slot
+    if (op.single_slot && !ops.empty() && ops.back().single_slot && ops.back().a == op.a) {
+      HostOp& pr = ops.back();
+      const cd* A = pr.m;
+      const cd* B = op.m;
+      cd Cm[4] = {B[0] * A[0] + B[1] * A[2], B[0] * A[1] + B[1] * A[3],
+                  B[2] * A[0] + B[3] * A[2], B[2] * A[1] + B[3] * A[3]};
+      for (int e = 0; e < 4; ++e) pr.m[e] = Cm[e];
+      return;
+    }
+    ops.push_back(op);
+  };
+
+  auto emit = [&](const Gate& g) -> bool {
     double gm[32];
     gate_matrix(g, gm);
     HostOp op;
@@ -178,42 +219,57 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
         int s = g.nq == 2 ? b : (b & 1);
         d[b] = cd(gm[2 * (s * dim + s)], gm[2 * (s * dim + s) + 1]);
       }
+      // factor out d[0] as a global phase (it commutes with every gate)
+      if (!is_one(d[0])) {
+        cd d0 = d[0];
+        gphase *= d0;
+        for (int b = 0; b < 4; ++b) d[b] /= d0;
+      }
       uint32_t r0 = ref(g.q0), r1 = g.nq == 2 ? ref(g.q1) : REF_NONE;
-      // canonical order: a slot first, and ascending slots
       bool swap01 = false;
       if (r1 != REF_NONE && is_slot(r1) && (!is_slot(r0) || r1 < r0)) swap01 = true;
       if (swap01) {
         std::swap(r0, r1);
         std::swap(d[1], d[2]);
       }
-      for (int e = 0; e < 4; ++e) op.m[e] = d[e];
-      if (is_slot(r0) && r1 != REF_NONE && is_slot(r1)) {
-        op.kind = PK_D2;
+      if (is_slot(r0) && r1 == REF_NONE) {  // one-slot diagonal: mergeable matrix
+        op.kind = PK_G1;
+        op.single_slot = true;
+        op.a = r0;
+        op.m[0] = d[0]; op.m[1] = 0; op.m[2] = 0; op.m[3] = d[1];
+      } else if (is_slot(r0) && is_slot(r1)) {
         op.a = r0;
         op.b = r1;
+        for (int e = 0; e < 4; ++e) op.m[e] = d[e];
+        if (is_one(d[0]) && is_one(d[1]) && is_one(d[2])) {
+          if (is_one(d[3])) return true;
+          op.kind = PK_D2P;
+        } else {
+          op.kind = PK_D2;
+        }
       } else if (is_slot(r0)) {
-        op.kind = PK_D1;
+        op.kind = PK_D1K;
         op.a = r0;
         op.b = r1;
-        op.single_slot = (r1 == REF_NONE);
+        for (int e = 0; e < 4; ++e) op.m[e] = d[e];
+        op.c = unit_mask(op.m);
       } else {
         op.kind = PK_D0;
         op.a = r0;
         op.b = r1;
+        for (int e = 0; e < 4; ++e) op.m[e] = d[e];
+        op.c = unit_mask(op.m);
+        if (op.c == 0xF) return true;
       }
-      op.c = unit_mask(op.m);
-    } else if (g.type == QS_CX || g.type == QS_X) {
-      op.kind = PK_XG;
-      int t = g.type == QS_CX ? g.q1 : g.q0;
-      op.a = ref(t);
-      op.b = g.type == QS_CX ? ref(g.q0) : REF_NONE;
-      op.single_slot = (op.b == REF_NONE);
-      op.m[0] = 0; op.m[1] = 1; op.m[2] = 1; op.m[3] = 0;
-    } else if (g.nq == 1) {
+    } else if (g.type == QS_CX) {
+      uint32_t t = ref(g.q1), c = ref(g.q0);
+      op.a = t;
+      op.b = c;
+      op.kind = is_slot(c) ? PK_XGS : PK_XGK;
+    } else if (g.nq == 1) {  // H, X, RX, U3
       op.kind = PK_G1;
-      op.a = ref(g.q0);
-      op.b = REF_NONE;
       op.single_slot = true;
+      op.a = ref(g.q0);
       for (int e = 0; e < 4; ++e) op.m[e] = cd(gm[2 * e], gm[2 * e + 1]);
     } else if (g.type == QS_SWAP) {
       op.kind = PK_SWAPR;
@@ -228,30 +284,7 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
     } else {
       return false;
     }
-    // merge consecutive uncontrolled one-slot ops on the same slot
-    if (op.single_slot && !ops.empty() && ops.back().single_slot && ops.back().a == op.a &&
-        ops.back().kind != PK_XCHG) {
-      HostOp& pr = ops.back();
-      cd A[4], B[4], Cm[4];
-      auto as_mat = [](const HostOp& o, cd* M) {
-        if (o.kind == PK_D1) {
-          M[0] = o.m[0]; M[1] = 0; M[2] = 0; M[3] = o.m[1];
-        } else {
-          for (int e = 0; e < 4; ++e) M[e] = o.m[e];
-        }
-      };
-      as_mat(pr, A);
-      as_mat(op, B);
-      Cm[0] = B[0] * A[0] + B[1] * A[2];
-      Cm[1] = B[0] * A[1] + B[1] * A[3];
-      Cm[2] = B[2] * A[0] + B[3] * A[2];
-      Cm[3] = B[2] * A[1] + B[3] * A[3];
-      pr.kind = PK_G1;
-      pr.b = REF_NONE;
-      for (int e = 0; e < 4; ++e) pr.m[e] = Cm[e];
-      return true;
-    }
-    ops.push_back(op);
+    push(op);
     return true;
   };
 
@@ -283,6 +316,7 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
     x.kind = PK_XCHG;
     x.map = cur;
     ops.push_back(x);
+    out->maps.push_back(cur);
     ++phases;
   }
   // store phase: register bits must avoid the low local bits
@@ -295,37 +329,85 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
     x.kind = PK_XCHG;
     x.map = cur;
     ops.push_back(x);
+    out->maps.push_back(cur);
     ++phases;
   }
   out->store = cur;
 
-  // serialise
+  // serialise; one-slot matrices take their cheapest form
   auto& w = out->prog;
-  for (const HostOp& o : ops) {
-    w.push_back(o.kind | (o.a << 8) | (o.b << 16) | (o.c << 24));
-    switch (o.kind) {
-      case PK_G1: push_floats(w, o.m, 4); break;
-      case PK_D1: case PK_D2: case PK_D0: push_floats(w, o.m, 4); break;
-      case PK_XX: {
-        float c = (float)o.x0, s = (float)o.x1;
-        uint32_t a, b;
-        std::memcpy(&a, &c, 4);
-        std::memcpy(&b, &s, 4);
-        w.push_back(a);
-        w.push_back(b);
-        break;
+  auto fl = [&](double v) {
+    float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    w.push_back(u);
+  };
+  int nops = 0;
+  for (HostOp o : ops) {
+    if (o.single_slot) {
+      cd* M = o.m;
+      if (is_zero(M[1]) && is_zero(M[2])) {  // diagonal: factor out M[0]
+        if (!is_one(M[0])) {
+          gphase *= M[0];
+          M[3] /= M[0];
+          M[0] = 1.0;
+        }
+        if (is_one(M[3])) continue;  // identity
+        w.push_back(PK_D1B | (o.a << 8));
+        fl(M[3].real());
+        fl(M[3].imag());
+      } else if (is_zero(M[0]) && is_zero(M[3]) && is_one(M[1]) && is_one(M[2])) {
+        w.push_back(PK_XG | (o.a << 8));
+      } else if (is_real(M[0]) && is_real(M[1]) && is_real(M[2]) && is_real(M[3])) {
+        w.push_back(PK_G1R | (o.a << 8));
+        for (int e = 0; e < 4; ++e) fl(M[e].real());
+      } else if (is_real(M[0]) && is_imag(M[1]) && is_imag(M[2]) && is_real(M[3])) {
+        w.push_back(PK_G1X | (o.a << 8));
+        fl(M[0].real());
+        fl(M[1].imag());
+        fl(M[2].imag());
+        fl(M[3].real());
+      } else {
+        w.push_back(PK_G1 | (o.a << 8));
+        if (out->g1_word < 0) out->g1_word = (int)w.size();
+        for (int e = 0; e < 4; ++e) {
+          fl(M[e].real());
+          fl(M[e].imag());
+        }
       }
-      case PK_XCHG: {
+      ++nops;
+      continue;
+    }
+    w.push_back(o.kind | (o.a << 8) | (o.b << 16) | (o.c << 24));
+    ++nops;
+    switch (o.kind) {
+      case PK_D1K: case PK_D2: case PK_D0:
+        for (int e = 0; e < 4; ++e) {
+          fl(o.m[e].real());
+          fl(o.m[e].imag());
+        }
+        break;
+      case PK_D2P:
+        fl(o.m[3].real());
+        fl(o.m[3].imag());
+        break;
+      case PK_XX:
+        fl(o.x0);
+        fl(o.x1);
+        break;
+      case PK_XCHG:
         w.back() = PK_XCHG | ((uint32_t)o.map.nt << 8);
         for (int i = 0; i < kRegBits; ++i) w.push_back(swz(1u << o.map.R[i]));
         for (int k = 0; k < o.map.nt; ++k)
           w.push_back((1u << o.map.T[k]) | (swz(1u << o.map.T[k]) << 16));
         break;
-      }
-      default: break;
+      default:
+        break;
     }
   }
   w.push_back(PK_END);
+  out->phase_re = gphase.real();
+  out->phase_im = gphase.imag();
 
   for (int i = 0; i < kRegBits; ++i) {
     out->ld_er[i] = swz(1u << out->load.R[i]);
@@ -340,9 +422,47 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
     out->st_pthr[k] = (k < out->store.nt) ? (1ull << sp.act[out->store.T[k]]) : 0;
   }
   out->num_phases = phases;
-  out->num_ops = (int)ops.size();
+  out->num_ops = nops;
   out->ok = true;
   return true;
+}
+
+// The global phases factored out of every phased program are applied once:
+// folded into the first general 2x2 op of the plan, else appended as a
+// scaling op to the last phased program.
+void fold_global_phase(std::vector<ShmProgramV2>& progs) {
+  cd total = 1.0;
+  int last = -1;
+  for (size_t i = 0; i < progs.size(); ++i)
+    if (progs[i].ok) {
+      total *= cd(progs[i].phase_re, progs[i].phase_im);
+      last = (int)i;
+    }
+  if (last < 0 || is_one(total)) return;
+  for (auto& pg : progs) {
+    if (!pg.ok || pg.g1_word < 0) continue;
+    for (int e = 0; e < 4; ++e) {
+      float re, im;
+      std::memcpy(&re, &pg.prog[pg.g1_word + 2 * e], 4);
+      std::memcpy(&im, &pg.prog[pg.g1_word + 2 * e + 1], 4);
+      cd v = cd(re, im) * total;
+      float nr = (float)v.real(), ni = (float)v.imag();
+      std::memcpy(&pg.prog[pg.g1_word + 2 * e], &nr, 4);
+      std::memcpy(&pg.prog[pg.g1_word + 2 * e + 1], &ni, 4);
+    }
+    return;
+  }
+  auto& w = progs[last].prog;
+  w.pop_back();  // PK_END
+  w.push_back(PK_SCALE);
+  float re = (float)total.real(), im = (float)total.imag();
+  uint32_t a, b;
+  std::memcpy(&a, &re, 4);
+  std::memcpy(&b, &im, 4);
+  w.push_back(a);
+  w.push_back(b);
+  w.push_back(PK_END);
+  progs[last].num_ops++;
 }
 
 }  // namespace qs

@@ -11,18 +11,29 @@ constexpr int kRegBits = 5;          // register qubits per thread: 32 amplitude
 constexpr int kRegAmps = 1 << kRegBits;
 constexpr int kMaxThreadBits = 9;    // 2^14 tile / 32 per thread = 512 threads
 constexpr int kMinPhasedM = 10;      // smaller tiles use the generic kernel
+constexpr int kMaxPhasedM = 14;      // 2^14 complex64 = 128 KiB tile
 
-// opcodes of the program stream (uint32 words; word 0 = op | a<<8 | b<<16 | c<<24)
+// opcodes of the program stream (uint32 words; word 0 = op | a<<8 | b<<16 | c<<24;
+// a, b are register slots 0..4 or qubit references, c a unit-entry mask)
 enum : uint32_t {
   PK_END = 0,
-  PK_G1 = 1,    // a = slot, b = control ref; 8 floats (2x2 complex)
-  PK_XG = 2,    // a = slot, b = control ref; swap the pair (X gate)
-  PK_D1 = 3,    // a = slot, b = known ref (or none), c = unit mask; 8 floats d[4]
-  PK_D2 = 4,    // a = slot0 < b = slot1, c = unit mask; 8 floats d[4]
-  PK_D0 = 5,    // a = known ref0, b = known ref1 (or none), c = unit mask; 8 floats
-  PK_SWAPR = 6, // a = slot0 < b = slot1
-  PK_XX = 7,    // a = slot0 < b = slot1; 2 floats (cos t/2, sin t/2)
-  PK_XCHG = 8,  // a = thread bits; 5 words er[], then nt words (tloc | tswz << 16)
+  PK_G1 = 1,      // a = slot; 8 floats: general 2x2 complex
+  PK_G1R = 2,     // a = slot; 4 floats: real 2x2
+  PK_G1X = 3,     // a = slot; 4 floats: u00 (real), u01 (imag), u10 (imag), u11 (real)
+  PK_G1C = 4,     // a = slot, b = control ref; 8 floats general 2x2
+  PK_XG = 5,      // a = slot: X (swap of the pair)
+  PK_XGS = 6,     // a = target slot, b = control slot
+  PK_XGK = 7,     // a = target slot, b = control ref known per thread
+  PK_D1 = 8,      // a = slot; 4 floats: e0, e1
+  PK_D1B = 9,     // a = slot; 2 floats: e1 on amplitudes with the bit set
+  PK_D1K = 10,    // a = slot, b = known ref, c = unit mask; 8 floats d[bit + 2 kb]
+  PK_D2 = 11,     // a = slot0 < b = slot1; 8 floats d[b0 + 2 b1]
+  PK_D2P = 12,    // a = slot0 < b = slot1; 2 floats: factor on b0 = b1 = 1
+  PK_D0 = 13,     // a = known ref0, b = known ref1 or none, c = unit mask; 8 floats
+  PK_SWAPR = 14,  // a = slot0 < b = slot1
+  PK_XX = 15,     // a = slot0 < b = slot1; 2 floats (cos t/2, sin t/2)
+  PK_SCALE = 16,  // 2 floats: every amplitude times a constant
+  PK_XCHG = 17,   // a = thread bits nt; 5 words er[], nt words (tloc | tswz << 16)
 };
 
 // qubit references inside an op
@@ -54,6 +65,24 @@ struct ShmProgramV2 {
   uint32_t ld_er[kRegBits], ld_tloc[kMaxThreadBits], ld_tswz[kMaxThreadBits];
   int num_phases = 0;        // exchanges + 1
   int num_ops = 0;
+  // global phase factored out of diagonal gates (applied once per plan)
+  double phase_re = 1.0, phase_im = 0.0;
+  int g1_word = -1;          // word index of the first general PK_G1's floats
+  // runs of non-active bits: batch index bits [src, src+len) -> physical dst
+  int nruns = 0;
+  uint8_t run_src[16], run_len[16], run_dst[16];
+  // every phase's map in program order: maps[0] = load map, maps[i] = the
+  // target of the i-th PK_XCHG (the last one is the store map)
+  std::vector<PhaseMap> maps;
+  int act[kMaxPhasedM];      // physical qubit of local bit j
+  int jit_module = -1;       // index of the JIT module holding this kernel, -1: none
 };
+
+// Padded shared-memory layout of the JIT kernels: one spare amplitude per 16,
+// 256 and 4096.  Additive over disjoint bit sets, so an address is a thread
+// part plus a compile-time register part; distinct residues mod 4 of the
+// four half-warp lane bits give distinct banks.
+inline uint32_t pad_index(uint32_t li) { return li + (li >> 4) + (li >> 8) + (li >> 12); }
+inline uint32_t pad_size(int m) { return pad_index((1u << m) - 1u) + 1u; }
 
 }  // namespace qs

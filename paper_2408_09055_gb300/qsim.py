@@ -59,7 +59,8 @@ class qs_plan_stats(ctypes.Structure):
                 ("num_shm", ctypes.c_uint64), ("num_fused", ctypes.c_uint64),
                 ("cost", ctypes.c_double), ("planner_ms", ctypes.c_double),
                 ("dp_states", ctypes.c_uint64), ("num_phased", ctypes.c_uint64),
-                ("num_exchanges", ctypes.c_uint64)]
+                ("num_exchanges", ctypes.c_uint64), ("num_jit", ctypes.c_uint64),
+                ("jit_ms", ctypes.c_double)]
 
 
 class qs_kernel_desc(ctypes.Structure):
@@ -91,6 +92,7 @@ def _load():
         "qs_plan_kernel_gates": ([vp, u64, ip, u64], i64),
         "qs_plan_fused_matrix": ([vp, u64, dp, u64], ctypes.c_int),
         "qs_plan_validate": ([vp, vp, u64], ctypes.c_int),
+        "qs_plan_kernel_source": ([vp, u64, ctypes.c_char_p, u64], i64),
         "qs_state_create": ([i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "qs_state_free": ([vp], None),
         "qs_state_device_ptr": ([vp], vp),
@@ -204,6 +206,12 @@ class Plan:
         check(_lib.qs_plan_fused_matrix(self.h, k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         out.size), "qs_plan_fused_matrix")
         return out.view(np.complex128).reshape(dim, dim)
+
+    def kernel_source(self, k: int) -> str:
+        n = check(_lib.qs_plan_kernel_source(self.h, k, None, 0), "qs_plan_kernel_source")
+        buf = ctypes.create_string_buffer(n + 1)
+        check(_lib.qs_plan_kernel_source(self.h, k, buf, n + 1), "qs_plan_kernel_source")
+        return buf.value.decode()
 
     def validate(self, gates=None) -> int:
         g = self._gates if gates is None else _gates_array(gates)

@@ -23,7 +23,7 @@ def gen(kind, n, seed):
 @pytest.mark.parametrize("kind", ["layered", "mixed", "entangling"])
 @pytest.mark.parametrize("algo", list(ALGOS))
 @pytest.mark.parametrize("n", [12, 17])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_shm_plans_match_oracle(kind, algo, n, variant):
     need_gpu()
     from paper_2408_09055_gb300 import qsim as Q
@@ -31,7 +31,8 @@ def test_shm_plans_match_oracle(kind, algo, n, variant):
     plan = Q.Plan(n, g, algo=ALGOS[algo], fuse_kmax=0, shm_variant=variant)
     assert plan.validate() == 0
     st = plan.stats()
-    assert st.num_phased == (st.num_shm if variant == 2 else 0)
+    assert st.num_phased == (st.num_shm if variant >= 2 else 0)
+    assert st.num_jit == (st.num_shm if variant == 3 else 0)
     got, _, _ = run_plan_on_gpu(n, plan)
     assert_close_state(got, sim.apply(n, g))
 
@@ -53,12 +54,13 @@ def test_fused_fp32_plans_match_oracle(kmax):
 
 
 @pytest.mark.parametrize("m", [10, 11, 12, 13, 14])
-def test_phased_kernel_every_tile_size(m):
+@pytest.mark.parametrize("variant", [2, 3])
+def test_phased_kernel_every_tile_size(m, variant):
     need_gpu()
     from paper_2408_09055_gb300 import qsim as Q
     n = 18
     g = C.concat(C.mixed_circuit(n, 700, m), C.entangling_circuit(n, 3, m))
-    plan = Q.Plan(n, g, algo=2, fuse_kmax=0, shm_max_active=m, shm_variant=2)
+    plan = Q.Plan(n, g, algo=2, fuse_kmax=0, shm_max_active=m, shm_variant=variant)
     st = plan.stats()
     assert st.num_phased == st.num_shm and st.num_exchanges > 0
     rng = np.random.default_rng(m)
