@@ -277,8 +277,11 @@ def main():
     pass_bytes = 16.0 * (1 << n)
     by_type = {}
     for k, d in enumerate(kdesc):
-        nm = ("shm_kernel_v2" if ps.num_phased else "shm_kernel_v1") if d.type == Q.QS_KERNEL_SHM \
-            else "fused_fp32_kernel"
+        if d.type == Q.QS_KERNEL_SHM:
+            nm = ("qsk<i> (plan-specialised shared-memory kernel)" if ps.num_jit else
+                  "shm_kernel_v2" if ps.num_phased else "shm_kernel_v1")
+        else:
+            nm = "fused_fp32_kernel"
         t = by_type.setdefault(nm, [0.0, 0])
         t[0] += per_kernel_ms[k]
         t[1] += runs
@@ -326,7 +329,7 @@ def main():
         "config": {"workload": WORKLOAD, "n_qubits": n, "gates": N_GATES, "plan": label,
                    "kernels": int(ps.num_kernels), "shm_kernels": int(ps.num_shm),
                    "fused_kernels": int(ps.num_fused), "passes": int(ps.num_kernels),
-                   "planner_ms": ps.planner_ms, "l2": "no flush: the 8 GiB state exceeds L2",
+                   "planner_ms": ps.planner_ms, "jit_ms": ps.jit_ms, "l2": "no flush: the 8 GiB state exceeds L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gates_per_s": N_GATES / (value * 1e-3),
         "hbm_roofline_frac_circuit": ps.num_kernels * pass_bytes / (value * 1e-3) / 1e9 / hbm,
