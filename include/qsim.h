@@ -232,6 +232,28 @@ int qs_remap(const float* in_device, float* out_device, int32_t n,
 int qs_apply_fused(float* state_device, int32_t n, const int32_t* targets,
                    int32_t k, const float* u_host, int32_t precision, void* stream);
 
+/* Allocation-free form of qs_apply_fused.  The paper has no counterpart:
+ * it exists for callers that must not allocate device memory while they
+ * apply a gate -- code that runs with every byte of device memory already
+ * handed to another allocator or budget, or that cannot accept the
+ * synchronisation and failure modes of an allocation in the middle of its
+ * work.  qs_apply_fused stages the 2^k x 2^k matrix in memory it allocates
+ * on every call; this entry point stages it in one fixed device array
+ * instead (128 KiB, held by every GPU that loads the library until the
+ * process exits), so it calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * Arguments, layout and results are those of qs_apply_fused.  Limit: k <= 7
+ * (2^7 x 2^7 complex64 fills the array); a larger k returns QS_EINVAL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the array, which
+ * keeps the last call's matrix; calls whose work overlaps on the GPU (for
+ * example from two host threads on two streams) race on it and must be
+ * serialised by the caller.  Synchronises the stream before returning.     */
+int qs_apply_fused_static(float* state_device, int32_t n, const int32_t* targets,
+                          int32_t k, const float* u_host, int32_t precision, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

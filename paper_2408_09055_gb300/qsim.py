@@ -108,6 +108,7 @@ def _load():
         "qs_state_compare_c128": ([vp, vp, dp, dp, vp], ctypes.c_int),
         "qs_remap": ([vp, vp, i32, ip, vp], ctypes.c_int),
         "qs_apply_fused": ([vp, i32, ip, i32, fp, i32, vp], ctypes.c_int),
+        "qs_apply_fused_static": ([vp, i32, ip, i32, fp, i32, vp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -308,3 +309,12 @@ def qs_apply_fused(state_ptr: int, n: int, targets, u: np.ndarray, precision: in
     check(_lib.qs_apply_fused(state_ptr, n, t, len(targets),
                               uu.view(np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                               precision, _stream_ptr(stream)), "qs_apply_fused")
+
+
+def qs_apply_fused_static(state_ptr: int, n: int, targets, u: np.ndarray, precision: int, stream=None):
+    """Allocation-free form of qs_apply_fused (k <= 7, shared static staging buffer)."""
+    t = (ctypes.c_int32 * len(targets))(*[int(x) for x in targets])
+    uu = np.ascontiguousarray(u, dtype=np.complex64)
+    check(_lib.qs_apply_fused_static(state_ptr, n, t, len(targets),
+                                     uu.view(np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                     precision, _stream_ptr(stream)), "qs_apply_fused_static")
