@@ -208,6 +208,25 @@ def make_plan(Q, gates, which, shm_max=13):
     return Q.Plan(N_QUBITS, gates, opts), label
 
 
+def profile_run(args):
+    """One untimed execution of the workload's plan at a smaller size."""
+    import torch
+    from paper_2408_09055_gb300 import qsim as Q
+    from synth import circuits as C
+    n = args.profile_run
+    gates = C.mixed_circuit(n, N_GATES, SEED)
+    opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=0, shm_max_active=args.shm_max)
+    plan = Q.Plan(n, gates, opts)
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    st = Q.State(n, buf.data_ptr())
+    s = torch.cuda.current_stream().cuda_stream
+    st.set_zero(s)
+    st.run(plan, s)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": n, "kernels": int(plan.stats().num_kernels), "norm2": st.norm2(s)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,7 +237,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--shm-max", type=int, default=13)
+    ap.add_argument("--profile-run", type=int, default=0, metavar="N",
+                    help="plan the workload's circuit generator at N qubits and run the plan "
+                         "once, untimed (a small case for profiler captures)")
     args = ap.parse_args()
+    if args.profile_run:
+        return profile_run(args)
     if args.impl == "reference":
         return reference_arm(args)
 
