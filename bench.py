@@ -198,11 +198,15 @@ def reference_arm(args):
     return 0
 
 
-def make_plan(Q, gates, which, shm_max=13):
-    if which == "A":
+def make_plan(Q, gates, which, shm_max=13, algo=None):
+    if which == "A" and algo == "ordered":
         opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, cost_kind=Q.QS_COST_ANALYTIC,
                               precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0)
-        label = "A: analytic-cost OrderedKernelize, shared-memory kernels, FP32"
+        label = "A': analytic-cost OrderedKernelize, shared-memory kernels, FP32"
+    elif which == "A":
+        opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, cost_kind=Q.QS_COST_ANALYTIC,
+                              precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0)
+        label = "A: analytic-cost Kernelize, shared-memory kernels, FP32"
     else:
         raise ValueError(which)
     return Q.Plan(N_QUBITS, gates, opts), label
@@ -215,7 +219,9 @@ def profile_run(args):
     from synth import circuits as C
     n = args.profile_run
     gates = C.mixed_circuit(n, N_GATES, SEED)
-    opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=0, shm_max_active=args.shm_max)
+    opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=args.shm_max)
+    if args.algo == "ordered":
+        opts.algo = Q.QS_ALGO_ORDERED
     plan = Q.Plan(n, gates, opts)
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     st = Q.State(n, buf.data_ptr())
@@ -234,6 +240,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plan", default="A")
+    ap.add_argument("--algo", default=None, choices=[None, "ordered", "kernelize"],
+                    help="override the plan's kernelization algorithm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--shm-max", type=int, default=13)
@@ -261,7 +269,7 @@ def main():
     from synth import circuits as C
 
     gates = C.mixed_circuit(N_QUBITS, N_GATES, SEED)
-    plan, label = make_plan(Q, gates, args.plan, args.shm_max)
+    plan, label = make_plan(Q, gates, args.plan, args.shm_max, args.algo)
     ps = plan.stats()
     kdesc = [plan.kernel(k) for k in range(ps.num_kernels)]
     n = N_QUBITS

@@ -114,7 +114,7 @@ typedef struct qs_plan_opts {
   const qs_mlp* mlp;         /* learned cost model (cost_kind = LEARNED)        */
 } qs_plan_opts;
 
-/* Fills `opts` with the defaults (Kernelize, analytic cost, FP32, |A| <= 12,
+/* Fills `opts` with the defaults (Kernelize, analytic cost, FP32, |A| <= 13,
  * 4 forced low qubits, fused k in [1, 6], T = 500, attach on, L = n).       */
 void qs_plan_opts_default(qs_plan_opts* opts);
 /* The built-in analytic cost table. */

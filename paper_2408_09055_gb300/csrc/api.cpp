@@ -150,10 +150,10 @@ void qs_cost_table_default(qs_cost_table* t) {
 void qs_plan_opts_default(qs_plan_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
-  o->algo = QS_ALGO_ORDERED;
+  o->algo = QS_ALGO_KERNELIZE;
   o->cost_kind = QS_COST_ANALYTIC;
   o->precision = QS_PREC_FP32;
-  o->shm_max_active = 12;
+  o->shm_max_active = 13;
   o->forced_low = 4;
   o->fuse_kmin = 1;
   o->fuse_kmax = 6;

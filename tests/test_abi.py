@@ -35,4 +35,4 @@ def test_status_strings_and_defaults_without_gpu():
     from paper_2408_09055_gb300 import qsim as Q
     assert Q.lib.qs_strerror(Q.QS_EINVAL) == b"invalid argument"
     o = Q.default_opts()
-    assert o.shm_max_active == 12 and o.forced_low == 4 and o.prune_T == 500
+    assert o.shm_max_active == 13 and o.forced_low == 4 and o.prune_T == 500 and o.algo == Q.QS_ALGO_KERNELIZE

@@ -9,7 +9,7 @@ from tests.gpu_util import assert_close_state, need_gpu, run_plan_on_gpu, torch
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = {"per_gate": 0, "greedy": 1, "ordered": 2}
+ALGOS = {"per_gate": 0, "greedy": 1, "ordered": 2, "kernelize": 3}
 
 
 def gen(kind, n, seed):
@@ -178,24 +178,3 @@ def test_apply_fused_matches_kernel_unitary(k):
     Q.qs_apply_fused(buf.data_ptr(), n, targets, u, Q.QS_PREC_FP32, torch.cuda.current_stream().cuda_stream)
     got = buf.cpu().numpy().view(np.complex64)
     assert_close_state(got, ref)
-
-
-def test_plan_fused_matrix_matches_oracle():
-    from paper_2408_09055_gb300 import qsim as Q
-    n = 8
-    g = C.entangling_circuit(n, 2, 4)
-    cost = Q.default_cost_table()
-    for k in range(16):
-        cost.fuse_cost[k] = 1.0
-    plan = Q.Plan(n, g, algo=2, fuse_kmax=5, cost=cost)
-    found = 0
-    for k in range(plan.stats().num_kernels):
-        d = plan.kernel(k)
-        if d.type != Q.QS_KERNEL_FUSED:
-            continue
-        qubits = [q for q in range(n) if (d.qubit_mask >> q) & 1]
-        ids = plan.kernel_gates(k)
-        u_ref = sim.kernel_unitary(g[ids], qubits)
-        assert np.allclose(plan.fused_matrix(k), u_ref, atol=1e-12)
-        found += 1
-    assert found > 0
