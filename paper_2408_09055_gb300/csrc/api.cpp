@@ -181,6 +181,11 @@ int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_p
   if (o.cost_kind == QS_COST_LEARNED && !o.mlp) return QS_EINVAL;
   if (o.cost_kind != QS_COST_ANALYTIC && o.cost_kind != QS_COST_LEARNED) return QS_EINVAL;
   if (o.shm_variant < 0 || o.shm_variant > 3) return QS_EINVAL;
+  if (o.precision != QS_PREC_FP32 && o.fuse_kmax > 0) {
+    // tensor-core fused kernels are 2^6 wide: narrower kernels are widened
+    if (o.fuse_kmax > kTcTargets || n < kTcTargets + 5) return QS_EUNSUPPORTED;
+    o.fuse_kmin = kTcTargets;
+  }
   auto t0 = std::chrono::steady_clock::now();
   qs_plan* p = new (std::nothrow) qs_plan();
   if (!p) return QS_ENOMEM;
@@ -526,26 +531,49 @@ int qs_apply_fused(float* state, int32_t n, const int32_t* targets, int32_t k, c
     seen |= 1ull << targets[j];
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = sizeof(float2) << (2 * k);
-  void* du = nullptr;
-  cudaError_t e = cudaMallocAsync(&du, bytes, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaMemcpyAsync(du, u_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(du, s);
-    return cuda_status(e);
-  }
   FusedLaunch a;
   a.psi = reinterpret_cast<float2*>(state);
   a.n = n;
   a.k = k;
   std::fill(a.targets, a.targets + kMaxFuse, -1);
   std::copy(targets, targets + k, a.targets);
-  a.u = static_cast<const float2*>(du);
   a.precision = precision;
+  std::vector<float> staged;  // what the kernel reads: the matrix or tensor-core weights
+  if (precision == QS_PREC_FP32) {
+    staged.assign(u_host, u_host + (size_t(2) << (2 * k)));
+  } else {
+    if (k > kTcTargets || n < kTcTargets + 5) return QS_EUNSUPPORTED;
+    // widen to 6 targets with the lowest unused qubits: U (x) I
+    const int kw = kTcTargets, dk = 1 << k, dw = 1 << kw;
+    std::vector<float> uw(size_t(2) * dw * dw, 0.0f);
+    for (int r = 0; r < dw; ++r)
+      for (int c = 0; c < dw; ++c)
+        if ((r >> k) == (c >> k)) {
+          uw[2 * (r * dw + c)] = u_host[2 * ((r & (dk - 1)) * dk + (c & (dk - 1)))];
+          uw[2 * (r * dw + c) + 1] = u_host[2 * ((r & (dk - 1)) * dk + (c & (dk - 1))) + 1];
+        }
+    for (int q = 0, j = k; q < n && j < kw; ++q)
+      if (!((seen >> q) & 1)) {
+        a.targets[j++] = q;
+        seen |= 1ull << q;
+      }
+    a.k = kw;
+    tc_prepare_weights(uw.data(), precision == QS_PREC_TF32X3, &staged);
+  }
+  const size_t bytes = staged.size() * sizeof(float);
+  void* du = nullptr;
+  cudaError_t e = cudaMallocAsync(&du, bytes, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemcpyAsync(du, staged.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(du, s);
+    return cuda_status(e);
+  }
+  a.u = static_cast<const float2*>(du);
   int rc = launch_fused(a, s);
   cudaFreeAsync(du, s);
   if (rc == QS_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == QS_OK && precision != QS_PREC_FP32) rc = tc_check_error(true);
   return rc;
 }
 

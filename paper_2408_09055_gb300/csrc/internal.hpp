@@ -68,6 +68,7 @@ struct FusedProgram {
   int targets[kMaxFuse];     // physical qubit of matrix index bit j
   std::vector<float> u;      // 2^k x 2^k complex64, row-major interleaved
   std::vector<double> u64;   // the FP64 product (kept for export / tests)
+  std::vector<float> w_tc;   // tensor-core weights (k = 6, TF32 / 3xTF32), else empty
 };
 
 struct DeviceCache {
@@ -140,6 +141,9 @@ struct FusedLaunch {
   int precision;
 };
 int launch_fused(const FusedLaunch& a, cudaStream_t s);
+constexpr int kTcTargets = 6;  // width of the tensor-core fused kernel
+void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out);
+int tc_check_error(bool clear);
 
 int launch_set_zero(float2* psi, int n, cudaStream_t s);
 int launch_norm2(const float2* psi, int n, double* out_host, cudaStream_t s);

@@ -354,10 +354,17 @@ int compile_programs(PlanImpl* p) {
         compile_shm_v2(p, k, p->shm[i], &p->shm2[i]);
       if (p->opts.shm_variant >= 2 && !p->shm2[i].ok) return QS_EUNSUPPORTED;
     } else {
-      int want = std::min(p->n, std::max(p->opts.fuse_kmin, std::popcount(k.mask)));
+      const bool tc = p->opts.precision != QS_PREC_FP32;
+      int kmin = tc ? std::max(p->opts.fuse_kmin, kTcTargets) : p->opts.fuse_kmin;
+      int want = std::min(p->n, std::max(kmin, std::popcount(k.mask)));
       k.mask = widen_fused(k.mask, p->n, want);
       if (std::popcount(k.mask) > kMaxFuse) return QS_EPLAN;
       compile_fused(p, k, &p->fused[i]);
+      if (tc) {
+        if (p->fused[i].k != kTcTargets) return QS_EUNSUPPORTED;
+        tc_prepare_weights(p->fused[i].u.data(), p->opts.precision == QS_PREC_TF32X3,
+                           &p->fused[i].w_tc);
+      }
     }
   }
   fold_global_phase(p->shm2);
