@@ -52,7 +52,12 @@ static int ensure_device(PlanImpl* p, DeviceCache** out) {
       dc.prog_off.push_back(poff);
     } else {
       dc.prog_off.push_back(0);
-      const auto& u = p->fused[i].u;
+      // tensor-core precisions read the prepared weights, FP32 the matrix
+      const bool tc = p->opts.precision != QS_PREC_FP32;
+      const auto& u = tc ? p->fused[i].w_tc : p->fused[i].u;
+      const size_t need = tc ? size_t(p->opts.precision == QS_PREC_TF32X3 ? 2 : 1) * 128 * 128
+                             : size_t(2) << (2 * p->fused[i].k);
+      if (u.size() != need) return QS_EPLAN;  // never hand a kernel a short buffer
       host.resize(off + u.size() * sizeof(float));
       std::memcpy(host.data() + off, u.data(), u.size() * sizeof(float));
     }
