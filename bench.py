@@ -199,6 +199,14 @@ def reference_arm(args):
 
 
 def make_plan(Q, gates, which, shm_max=13, algo=None):
+    if which.startswith("F-"):  # every kernel fused (k = 6), in the given precision
+        prec = {"F-FP32": Q.QS_PREC_FP32, "F-TF32": Q.QS_PREC_TF32, "F-TF32X3": Q.QS_PREC_TF32X3}[which]
+        cost = Q.default_cost_table()
+        for k in range(16):
+            cost.fuse_cost[k] = 1.0
+        opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=prec, fuse_kmax=6, fuse_kmin=6,
+                              cost=cost)
+        return Q.Plan(N_QUBITS, gates, opts), f"{which}: Kernelize, every kernel a fused 2^6 unitary"
     if which == "A" and algo == "ordered":
         opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, cost_kind=Q.QS_COST_ANALYTIC,
                               precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0)
@@ -210,6 +218,15 @@ def make_plan(Q, gates, which, shm_max=13, algo=None):
     else:
         raise ValueError(which)
     return Q.Plan(N_QUBITS, gates, opts), label
+
+
+def workload_gates(name):
+    from synth import circuits as C
+    if name == "mixed":
+        return C.mixed_circuit(N_QUBITS, N_GATES, SEED)
+    if name == "entangling":
+        return C.entangling_circuit(N_QUBITS, 40, SEED)
+    raise ValueError(name)
 
 
 def profile_run(args):
@@ -245,6 +262,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--shm-max", type=int, default=13)
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "entangling"])
     ap.add_argument("--profile-run", type=int, default=0, metavar="N",
                     help="plan the workload's circuit generator at N qubits and run the plan "
                          "once, untimed (a small case for profiler captures)")
@@ -268,7 +286,7 @@ def main():
     from paper_2408_09055_gb300 import qsim as Q
     from synth import circuits as C
 
-    gates = C.mixed_circuit(N_QUBITS, N_GATES, SEED)
+    gates = workload_gates(args.workload)
     plan, label = make_plan(Q, gates, args.plan, args.shm_max, args.algo)
     ps = plan.stats()
     kdesc = [plan.kernel(k) for k in range(ps.num_kernels)]
@@ -313,7 +331,7 @@ def main():
             nm = ("qsk<i> (plan-specialised shared-memory kernel)" if ps.num_jit else
                   "shm_kernel_v2" if ps.num_phased else "shm_kernel_v1")
         else:
-            nm = "fused_fp32_kernel"
+            nm = "fused_fp32_kernel" if plan.opts.precision == Q.QS_PREC_FP32 else "fused_tc_kernel"
         t = by_type.setdefault(nm, [0.0, 0])
         t[0] += per_kernel_ms[k]
         t[1] += runs
@@ -358,12 +376,15 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_qubits": n, "gates": N_GATES, "plan": label,
+        "config": {"workload": WORKLOAD if args.workload == "mixed" else
+                   f"entangling circuit, {n} qubits, 40 layers (U3 on every qubit, CP+RXX on a random "
+                   f"matching), seed {SEED}",
+                   "n_qubits": n, "gates": int(len(gates)), "plan": label,
                    "kernels": int(ps.num_kernels), "shm_kernels": int(ps.num_shm),
                    "fused_kernels": int(ps.num_fused), "passes": int(ps.num_kernels),
                    "planner_ms": ps.planner_ms, "jit_ms": ps.jit_ms, "l2": "no flush: the 8 GiB state exceeds L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "gates_per_s": N_GATES / (value * 1e-3),
+        "gates_per_s": len(gates) / (value * 1e-3),
         "hbm_roofline_frac_circuit": ps.num_kernels * pass_bytes / (value * 1e-3) / 1e9 / hbm,
         "roofline": roof,
         "gpu_launches": int(sum(v[1] for v in by_type.values())) * 1,
@@ -375,6 +396,8 @@ def main():
                 "norm2_out": e2e_norm},
     }
     del host_in, host_out
+    if plan.opts.precision != Q.QS_PREC_FP32:
+        line["dtype"] = {Q.QS_PREC_TF32: "tf32", Q.QS_PREC_TF32X3: "tf32x3"}[plan.opts.precision]
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, thr = oracle_sample(gates, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "ms/circuit", "cores": thr, "kind": "oracle",

@@ -445,17 +445,23 @@ int jit_compile_plan(PlanImpl* p) {
     if (p->shm2[i].ok) idx.push_back((int)i);
   p->jit_modules.clear();
   if (idx.empty()) return QS_OK;
-  const int per_module = 8;
-  const int nmod = (int)((idx.size() + per_module - 1) / per_module);
-  std::vector<std::string> srcs(nmod);
-  std::vector<std::vector<int>> members(nmod);
-  for (size_t t = 0; t < idx.size(); ++t) {
-    int i = idx[t];
+  // modules of at most ~64 KB of source (a large kernel gets its own module):
+  // front-end and ptxas time grow faster than linearly with module size, and
+  // more modules spread over more threads
+  const size_t budget = 64 * 1024;
+  std::vector<std::string> srcs;
+  std::vector<std::vector<int>> members;
+  for (int i : idx) {
     std::string name = "qsk" + std::to_string(i), s;
     if (!jit_source(p->shm2[i], p->n, name, &s)) continue;
-    srcs[t / per_module] += s;
-    members[t / per_module].push_back(i);
+    if (srcs.empty() || srcs.back().size() + s.size() > budget) {
+      srcs.emplace_back();
+      members.emplace_back();
+    }
+    srcs.back() += s;
+    members.back().push_back(i);
   }
+  const int nmod = (int)srcs.size();
   p->jit_modules.assign(nmod, std::vector<char>());
   std::vector<char> ok(nmod, 0);
   std::atomic<int> next{0};
