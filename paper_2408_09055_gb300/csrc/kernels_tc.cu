@@ -129,7 +129,7 @@ __host__ __device__ constexpr uint32_t core_off(uint32_t m, uint32_t kk) {
 }
 
 template <int CB, bool X3>
-__global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_constant__ TcParams P) {
+__global__ void __launch_bounds__(kTcThreads, X3 ? 1 : 2) fused_tc_kernel(const __grid_constant__ TcParams P) {
   constexpr int N = 1 << CB;
   constexpr uint32_t A_FLOATS = kTcKR * kTcKR;
   constexpr uint32_t B_FLOATS = N * kTcKR;
@@ -182,26 +182,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
   const uint32_t tmem = tmem_base;
   uint32_t parity = 0;
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
-  for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x) {
+  constexpr int E = kTcDim * N / kTcThreads;  // tile elements per thread
+  const int lane = tid & 31;
+  auto tile_base = [&](uint64_t bt) {
     uint64_t base = 0, x = bt;
     for (int q = 0; q < P.n && x; ++q)
       if (!((P.fixed >> q) & 1ull)) {
         base |= (x & 1ull) << q;
         x >>= 1;
       }
-    // state tile -> B operand (real block rows: Re 0..63, Im 64..127)
-    for (int e = tid; e < kTcDim * N; e += kTcThreads) {
-      const int lane = e & 31, wq = e >> 5;
-      const int c = (lane & 7) + 8 * (wq % (N / 8));
-      const int j = (lane >> 3) + 4 * (wq / (N / 8));
-      const float2 v = P.psi[base | rowoff[j] | coloff[c]];
+    return base;
+  };
+  // element i of this thread: column c, row j (8 consecutive columns x 4 rows
+  // per warp access: 64-byte global runs, conflict-free operand stores)
+  auto elem = [&](int i, int& c, int& j) {
+    const int wq = (tid >> 5) + (kTcThreads / 32) * i;
+    c = (lane & 7) + 8 * (wq % (N / 8));
+    j = (lane >> 3) + 4 * (wq / (N / 8));
+  };
+  float2 v[E];
+  auto load_tile = [&](uint64_t base) {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      int c, j;
+      elem(i, c, j);
+      v[i] = P.psi[base | rowoff[j] | coloff[c]];
+    }
+  };
+  // registers -> B operand (real block rows: Re 0..63, Im 64..127), then MMAs
+  auto stage_and_issue = [&]() {
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      int c, j;
+      elem(i, c, j);
       const uint32_t ore = core_off(c, j) >> 2, oim = core_off(c, j + kTcDim) >> 2;
-      const float hr = tf32_rna(v.x), hi = tf32_rna(v.y);
+      const float hr = tf32_rna(v[i].x), hi = tf32_rna(v[i].y);
       Bh[ore] = hr;
       Bh[oim] = hi;
       if (X3) {
-        Bl[ore] = v.x - hr;
-        Bl[oim] = v.y - hi;
+        Bl[ore] = v[i].x - hr;
+        Bl[oim] = v[i].y - hi;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -221,6 +241,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
       }
       mma_commit(mb);
     }
+  };
+  uint64_t bt = blockIdx.x;
+  uint64_t base = 0;
+  if (bt < nb) {
+    base = tile_base(bt);
+    load_tile(base);
+    stage_and_issue();
+  }
+  for (; bt < nb; bt += gridDim.x) {
+    // loads of the next tile are in flight while this tile's MMAs finish and
+    // its accumulator drains
+    const uint64_t nxt = bt + gridDim.x;
+    uint64_t nbase = 0;
+    if (nxt < nb) {
+      nbase = tile_base(nxt);
+      load_tile(nbase);
+    }
     const bool ok = mbar_wait(mb, parity);
     parity ^= 1u;
     if (!ok) abort_all = 1;
@@ -233,7 +270,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
     }
     {  // accumulator (row = TMEM lane) -> staging tile; warps w and w+4 share lanes
       const int lane_base = 32 * (warp & 3);
-      const int row = lane_base + (tid & 31);
+      const int row = lane_base + lane;
       const int c0 = (warp >> 2) * (N / 2);
 #pragma unroll 1
       for (int cc = 0; cc < N / 2; cc += 16) {
@@ -249,7 +286,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
       const int c = e & (N - 1), j = e >> CB;
       P.psi[base | rowoff[j] | coloff[c]] = make_float2(Dsm[j * DP + c], Dsm[(j + kTcDim) * DP + c]);
     }
-    __syncthreads();
+    __syncthreads();  // the staging tile (B region) is free again
+    if (nxt < nb) {
+      base = nbase;
+      stage_and_issue();
+    }
   }
   __syncthreads();
   if (warp == 0)
@@ -281,7 +322,8 @@ int launch_tc(const TcParams& P, cudaStream_t s) {
     if (dev < 32) attr_done |= 1u << dev;
   }
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
-  const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms);
+  const int per_sm = (2 * (smem + 4096) <= 228u * 1024u) ? 2 : 1;
+  const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms * per_sm);
   fused_tc_kernel<CB, X3><<<(unsigned)grid, kTcThreads, smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -347,7 +389,7 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
     P.targets[j] = (int8_t)a.targets[j];
     P.fixed |= 1ull << a.targets[j];
   }
-  const int cb = std::min(x3 ? 6 : 7, a.n - kTcK);
+  const int cb = std::min(6, a.n - kTcK);  // 64 columns per tile
   int got = 0;
   for (int q = 0; q < a.n && got < cb; ++q)
     if (!((P.fixed >> q) & 1ull)) P.cols[got++] = (int8_t)q;
@@ -358,8 +400,7 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
     return launch_tc<6, true>(P, s);
   }
   if (cb == 5) return launch_tc<5, false>(P, s);
-  if (cb == 6) return launch_tc<6, false>(P, s);
-  return launch_tc<7, false>(P, s);
+  return launch_tc<6, false>(P, s);
 }
 
 }  // namespace qs
