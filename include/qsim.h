@@ -232,6 +232,43 @@ int qs_remap(const float* in_device, float* out_device, int32_t n,
 int qs_apply_fused(float* state_device, int32_t n, const int32_t* targets,
                    int32_t k, const float* u_host, int32_t precision, void* stream);
 
+/* ---- learned kernel-cost model (a3, a9) -----------------------------------
+ * A three-layer perceptron (features -> hidden -> hidden -> 1, ReLU) that
+ * predicts ln(kernel time in microseconds on a 30-qubit state) from a
+ * kernel's features (qs_kernel_features).  Parameters live in device memory
+ * of the current device, FP32 (layout W1[F x H], b1[H], W2[H x H], b2[H],
+ * W3[H], b3[1], row-major).  Training runs the library's FP32-accumulate
+ * forward, backpropagation and Adam kernels; inference can use the BF16
+ * copy of the weights (BF16 activations, FP32 accumulation).  With
+ * qs_plan_opts.cost_kind = QS_COST_LEARNED the planners use exp(prediction)
+ * scaled by 2^(n-30) as a kernel's cost (feasibility rules unchanged).     */
+#define QS_MLP_FEATURES 44
+int qs_mlp_create(int32_t features, int32_t hidden, uint64_t seed, qs_mlp** out);
+void qs_mlp_free(qs_mlp* mlp);
+int64_t qs_mlp_num_params(const qs_mlp* mlp);
+int qs_mlp_shape(const qs_mlp* mlp, int32_t* features, int32_t* hidden);
+int qs_mlp_get_params(const qs_mlp* mlp, float* host_out, uint64_t n);
+/* Sets the parameters and resets the optimiser state. */
+int qs_mlp_set_params(qs_mlp* mlp, const float* host_in, uint64_t n);
+/* x: device [batch x features] FP32, t: device [batch] targets.  Gradient of
+ * the mean squared error into grad_out (host, num_params floats, or NULL);
+ * the loss into loss_out (host, or NULL).  Synchronises the stream.        */
+int qs_mlp_gradient(qs_mlp* mlp, const float* x_device, const float* t_device, int32_t batch,
+                    float* grad_out, float* loss_out, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch's gradient. */
+int qs_mlp_train_step(qs_mlp* mlp, const float* x_device, const float* t_device, int32_t batch,
+                      float lr, float* loss_out, void* stream);
+/* y (device [batch]) = network(x); bf16 != 0 uses the BF16 weights. Async. */
+int qs_mlp_forward(qs_mlp* mlp, const float* x_device, int32_t batch, float* y_device,
+                   int32_t bf16, void* stream);
+/* Host-side features of one kernel: bits 0..29 the kernel's qubit mask (its
+ * active set for a shared-memory kernel, its targets for a fused one),
+ * 30..39 gate counts per type / 16, 40 insular-gate count / 16, 41 the
+ * kernel type, 42 |mask| / 16, 43 gate count / 64.  out: QS_MLP_FEATURES
+ * floats.                                                                   */
+int qs_kernel_features(int32_t n, const qs_gate* gates, uint64_t ngates, int32_t kernel_type,
+                       uint64_t qubit_mask, float* out);
+
 /* Allocation-free form of qs_apply_fused.  The paper has no counterpart:
  * it exists for callers that must not allocate device memory while they
  * apply a gate -- code that runs with every byte of device memory already

@@ -1,0 +1,175 @@
+"""Learned kernel-cost model: timing data from this simulator on the GPU,
+training with the library's own kernels, save/load.
+
+Every sample is one kernel of the kind the planners emit, timed as the
+library executes it on a resident 30-qubit state:
+
+* shared-memory samples: a random subcircuit (an active set of 1..10 of the
+  30 qubits, 1..64 gates of the mixed gate set inside it), planned as a single
+  shared-memory kernel and compiled to its specialised form;
+* fused samples: a random subcircuit on 1..6 qubits applied as one fused
+  unitary in the requested precision.
+
+Features come from ``qs_kernel_features`` of the kernel as planned; the
+target is ln(microseconds).  Training runs ``qs_mlp_train_step`` (the
+library's FP32 forward/backward/Adam kernels) on mini-batches; inference in
+the planners uses the BF16 weights.  This module only marshals arguments and
+orchestrates; all arithmetic runs in libqsim's kernels.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import qsim as Q
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+MODEL_PATH = os.path.join(PKG, "data", "costmodel_gb300.npz")
+N_REF = 30  # state size the timings are taken on
+
+
+def _sample_specs(n, count, seed, fused_fraction, precision):
+    from synth import circuits as C
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        sub_seed = int(rng.integers(0, 2 ** 62))
+        fused = rng.uniform() < fused_fraction
+        if fused:
+            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=6)
+            cost = Q.default_cost_table()
+            for k in range(16):
+                cost.fuse_cost[k] = 1.0
+            opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=6, precision=precision, cost=cost)
+        else:
+            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=10)
+            opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=0, shm_max_active=14)
+        specs.append((g, opts, opts.cost))
+    return specs
+
+
+def _build(n, spec):
+    g, opts, _keep = spec
+    plan = Q.Plan(n, g, opts)
+    if plan.stats().num_kernels != 1:
+        return None
+    return plan
+
+
+def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.2, precision=Q.QS_PREC_TF32X3,
+             reps=3, batch=256, threads=None, stream=None, log=print):
+    """Times `count` random kernels; returns (X [count x F], y = ln(us), meta)."""
+    import torch
+    threads = threads or os.cpu_count() or 4
+    specs = _sample_specs(n, count, seed, fused_fraction, precision)
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    st = Q.State(n, buf.data_ptr())
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    st.set_zero(s)
+    X, y, kinds = [], [], []
+    t0 = time.time()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for b0 in range(0, len(specs), batch):
+            part = specs[b0:b0 + batch]
+            plans = list(ex.map(lambda sp: _build(n, sp), part))
+            for sp, plan in zip(part, plans):
+                if plan is None:
+                    continue
+                d = plan.kernel(0)
+                ids = plan.kernel_gates(0)
+                st.run(plan, s)  # warm-up: uploads and loads the kernel
+                timer = Q.Timer(plan, reps)
+                for _ in range(reps):
+                    st.run_timed(plan, timer, s)
+                ms, runs = timer.read()
+                X.append(Q.qs_kernel_features(n, sp[0][ids], d.type, d.qubit_mask))
+                y.append(math.log(ms[0] / runs * 1e3))
+                kinds.append(d.type)
+            del plans
+            if log:
+                log(f"timed {min(b0 + batch, len(specs))}/{len(specs)} kernels, {time.time() - t0:.0f} s")
+    meta = {"n": n, "count": len(y), "seed": seed, "fused_fraction": fused_fraction,
+            "precision": int(precision), "reps": reps, "seconds": time.time() - t0,
+            "fused_samples": int(sum(1 for k in kinds if k == Q.QS_KERNEL_FUSED))}
+    return np.asarray(X, dtype=np.float32), np.asarray(y, dtype=np.float32), meta
+
+
+def split(count, seed=0, fractions=(0.8, 0.1, 0.1)):
+    perm = np.random.default_rng(seed).permutation(count)
+    a = int(fractions[0] * count)
+    b = a + int(fractions[1] * count)
+    return perm[:a], perm[a:b], perm[b:]
+
+
+def train(X, y, hidden=128, epochs=200, batch=256, lr=1e-3, seed=0, stream=None, log=None):
+    """Trains a fresh network on (X, y) with an 80/10/10 split; returns the
+    network and a metrics dict (MSE of ln time; mean |relative error| of
+    time) for the train, validation and test parts."""
+    import torch
+    tr, va, te = split(len(y), seed)
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
+    yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).to(dev)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    net = Q.Mlp(X.shape[1], hidden, seed)
+    # centre the output on the mean target so training starts close
+    theta = net.get_params()
+    theta[-1] = float(np.mean(y[tr]))
+    net.set_params(theta)
+    rng = np.random.default_rng(seed + 1)
+    best, best_theta = float("inf"), net.get_params()
+    for ep in range(epochs):
+        order = tr[rng.permutation(len(tr))]
+        for b0 in range(0, len(order), batch):
+            idx = torch.from_numpy(order[b0:b0 + batch]).to(dev)
+            xb = Xd.index_select(0, idx).contiguous()
+            tb = yd.index_select(0, idx).contiguous()
+            net.train_step(xb.data_ptr(), tb.data_ptr(), len(idx), lr, s)
+        if ep % 10 == 9 or ep == epochs - 1:
+            v = evaluate(net, X[va], y[va], stream=s)["mse"]
+            if v < best:
+                best, best_theta = v, net.get_params()
+            if log:
+                log(f"epoch {ep + 1}: validation MSE {v:.4f}")
+    net.set_params(best_theta)
+    metrics = {name: evaluate(net, X[ix], y[ix], stream=s) for name, ix in
+               (("train", tr), ("validation", va), ("test", te))}
+    return net, metrics
+
+
+def predict(net, X, bf16=True, stream=None) -> np.ndarray:
+    import torch
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
+    out = torch.empty(len(X), dtype=torch.float32, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    net.forward(Xd.data_ptr(), len(X), out.data_ptr(), bf16, s)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def evaluate(net, X, y, bf16=True, stream=None) -> dict:
+    if len(y) == 0:
+        return {"mse": float("nan"), "mean_rel_err": float("nan")}
+    p = predict(net, X, bf16, stream)
+    rel = np.abs(np.exp(p - y) - 1.0)
+    return {"mse": float(np.mean((p - y) ** 2)), "mean_rel_err": float(np.mean(rel)),
+            "median_rel_err": float(np.median(rel))}
+
+
+def save(net, path=MODEL_PATH, meta=None) -> None:
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, theta=net.get_params(), features=net.features, hidden=net.hidden,
+             meta=json.dumps(meta or {}))
+
+
+def load(path=MODEL_PATH):
+    d = np.load(path)
+    net = Q.Mlp(int(d["features"]), int(d["hidden"]))
+    net.set_params(d["theta"])
+    return net, json.loads(str(d["meta"]))

@@ -2,6 +2,7 @@
 // libqsim.  Not part of the public ABI (see include/qsim.h).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -33,6 +34,8 @@ void gate_matrix(const Gate& g, double* m);
 // Validates a public gate and fills the internal one.  Returns QS_OK/EINVAL.
 int make_gate(const qs_gate& in, int n, Gate* out);
 bool gate_is_diagonal(int type);
+
+struct LearnedCost;  // learned.cpp
 
 // ---- plan ----------------------------------------------------------------
 struct Kernel {
@@ -93,18 +96,56 @@ struct PlanImpl {
   std::string jit_log;              // first NVRTC error log, if any
   double jit_ms = 0;
   double planner_ms = 0, total_cost = 0;
+  LearnedCost* learned = nullptr;  // set while planning with QS_COST_LEARNED
   uint64_t dp_states = 0;
   std::mutex mu;
   std::vector<DeviceCache> dev;     // one per device the plan ran on
 };
 
 // ---- planner (planner.cpp) --------------------------------------------------
+// What a kernel's cost depends on: its qubits, non-insular qubits, gate
+// counts per type, insular-gate count and gate count (and, for the analytic
+// model, the sum of per-gate costs).
+struct KStat {
+  uint64_t q = 0, ni = 0;
+  uint16_t cnt[QS_NUM_GATE_TYPES] = {};
+  uint16_t nins = 0, ng = 0;
+  double gcost = 0;
+  void add(const Gate& g, double gc) {
+    q |= g.qmask;
+    ni |= g.nimask;
+    if (cnt[g.type] < 0xFFFF) cnt[g.type]++;
+    if ((g.qmask & ~g.nimask) && nins < 0xFFFF) nins++;
+    if (ng < 0xFFFF) ng++;
+    gcost += gc;
+  }
+  void merge(const KStat& o) {
+    q |= o.q;
+    ni |= o.ni;
+    for (int t = 0; t < QS_NUM_GATE_TYPES; ++t) cnt[t] = (uint16_t)std::min(0xFFFF, cnt[t] + o.cnt[t]);
+    nins = (uint16_t)std::min(0xFFFF, nins + o.nins);
+    ng = (uint16_t)std::min(0xFFFF, ng + o.ng);
+    gcost += o.gcost;
+  }
+};
+
 struct CostModel {
   const PlanImpl* plan;
-  double fusion(uint64_t qmask) const;                  // INF if infeasible
-  double shm(uint64_t nimask, double gate_cost_sum) const;
+  LearnedCost* learned = nullptr;
+  double fusion(const KStat& s) const;  // INF if infeasible
+  double shm(const KStat& s) const;     // INF if infeasible
   double gate_cost(int type) const { return plan->cost.gate_cost[type]; }
+  // batches the learned predictions of these kernels (no-op for analytic)
+  void prefetch(const std::vector<std::pair<KStat, bool>>& ks) const;
 };
+// learned.cpp
+LearnedCost* learned_create(const PlanImpl* p, qs_mlp* mlp, int* status);
+void learned_destroy(LearnedCost* lc);
+double learned_cost(LearnedCost* lc, const KStat& s, bool fusion);
+void learned_prefetch(LearnedCost* lc, const std::vector<std::pair<KStat, bool>>& ks);
+int learned_status(const LearnedCost* lc);
+uint64_t widen_mask(uint64_t mask, int n, int want);
+void kernel_features(int n, const KStat& s, bool fusion, uint64_t exec_mask, float* out);
 int plan_kernels(PlanImpl* p);         // fills p->kernels
 int compile_programs(PlanImpl* p);     // fills p->shm / p->fused
 int validate_plan(const PlanImpl* p);  // Theorem 2 check

@@ -42,15 +42,15 @@ constexpr uint64_t ALLQ = ~0ull;  // ExtQ = all qubits
 
 struct Unit {
   std::vector<int32_t> gates;  // circuit indices in order
-  uint64_t q = 0, ni = 0;
-  double gcost = 0;
+  KStat st;
 };
 
 struct OpenK {
   uint8_t fusion = 0;
-  uint64_t q = 0, ni = 0;
+  uint64_t q = 0, ni = 0;  // mirrors of st.q / st.ni for the hot comparisons
   uint64_t ext = ALLQ;
-  double gcost = 0;
+  KStat st;
+  double cost = 0;         // the kernel's cost as it stands
   int32_t id = -1;
   bool operator<(const OpenK& o) const {
     if (fusion != o.fusion) return fusion < o.fusion;
@@ -85,14 +85,7 @@ struct Ctx {
   std::vector<uint8_t> kfusion;  // kernel id -> type
   int32_t next_id = 0;
 
-  double kcost(const OpenK& k) const {
-    if (k.fusion) {
-      int w = std::popcount(k.q);
-      int we = std::max(w, std::min(kmin, p->n));
-      return p->cost.fuse_cost[we];
-    }
-    return p->cost.alpha + k.gcost;
-  }
+  double kcost(const OpenK& k) const { return k.fusion ? cm.fusion(k.st) : cm.shm(k.st); }
   bool fits(const OpenK& k) const {
     if (k.fusion) return std::popcount(k.q) <= kmax;
     return std::popcount(k.ni | low) <= shm_max;
@@ -109,10 +102,10 @@ struct Ctx {
 
 // Can unit u be appended to open kernel k (extensibility + size)?
 bool admits(const Ctx& c, const OpenK& k, const Unit& u) {
-  if (k.ext != ALLQ && (u.q & ~k.ext)) return false;  // Constraint 1 via ExtQ
+  if (k.ext != ALLQ && (u.st.q & ~k.ext)) return false;  // Constraint 1 via ExtQ
   OpenK t = k;
-  t.q |= u.q;
-  t.ni |= u.ni;
+  t.q |= u.st.q;
+  t.ni |= u.st.ni;
   return c.fits(t);
 }
 
@@ -140,7 +133,7 @@ double pack(Ctx& c, std::vector<OpenK> ks, bool rec, int32_t* hist) {
         OpenK m = a;
         m.q |= b.q;
         m.ni |= b.ni;
-        m.gcost += b.gcost;
+        m.st.merge(b.st);
         if (!c.fits(m)) continue;
         if (c.kcost(m) >= c.kcost(a) + c.kcost(b)) continue;
         if (rec) *hist = c.push(1, b.id, a.id, *hist);
@@ -181,7 +174,7 @@ bool same_kernels(const std::vector<OpenK>& a, const std::vector<OpenK>& b) {
 // next multi-qubit gate on its qubit (else the previous one); when a qubit
 // has no multi-qubit gate at all, its gates join the closest multi-qubit gate
 // of the circuit.  Without multi-qubit gates each gate is its own unit.
-std::vector<Unit> make_units(const PlanImpl* p, const CostModel& cm, bool attach) {
+std::vector<Unit> make_units(const PlanImpl* p, bool attach) {
   const int L = (int)p->gates.size();
   std::vector<int> owner(L, -1);
   std::vector<int> multi;
@@ -229,9 +222,7 @@ std::vector<Unit> make_units(const PlanImpl* p, const CostModel& cm, bool attach
   for (int i = 0; i < L; ++i) {
     Unit& u = units[anchor_unit[owner[i]]];
     u.gates.push_back(i);
-    u.q |= p->gates[i].qmask;
-    u.ni |= p->gates[i].nimask;
-    u.gcost += cm.gate_cost(p->gates[i].type);
+    u.st.add(p->gates[i], p->cost.gate_cost[p->gates[i].type]);
   }
   return units;
 }
@@ -256,11 +247,11 @@ void compact(Ctx& c, std::vector<State>& states) {
 }  // namespace
 
 int plan_kernelize(PlanImpl* p) {
-  Ctx c{p, CostModel{p}, 0, p->opts.shm_max_active, p->opts.fuse_kmax, p->opts.fuse_kmin, {}, {}, 0};
+  Ctx c{p, CostModel{p, p->learned}, 0, p->opts.shm_max_active, p->opts.fuse_kmax, p->opts.fuse_kmin, {}, {}, 0};
   c.low = (p->opts.forced_low <= 0) ? 0ull
           : ((1ull << std::min(p->opts.forced_low, p->n)) - 1);
   const bool attach = p->opts.attach_single != 0;
-  std::vector<Unit> units = make_units(p, c.cm, attach);
+  std::vector<Unit> units = make_units(p, attach);
   const size_t T = p->opts.prune_T > 0 ? (size_t)p->opts.prune_T : std::numeric_limits<size_t>::max();
 
   std::vector<State> cur(1);
@@ -269,6 +260,18 @@ int plan_kernelize(PlanImpl* p) {
     const Unit& u = units[ui];
     // pruning: rank by cost after packing, keep the best T/2
     if (cur.size() >= T) {
+      if (c.cm.learned) {  // the packing below costs merges of all-extensible pairs
+        std::vector<std::pair<KStat, bool>> want;
+        for (const State& s : cur)
+          for (size_t i = 0; i < s.ks.size(); ++i)
+            for (size_t j = i + 1; j < s.ks.size(); ++j)
+              if (s.ks[i].ext == ALLQ && s.ks[j].ext == ALLQ && s.ks[i].fusion == s.ks[j].fusion) {
+                KStat m = s.ks[i].st;
+                m.merge(s.ks[j].st);
+                want.push_back({m, s.ks[i].fusion != 0});
+              }
+        c.cm.prefetch(want);
+      }
       std::vector<std::pair<double, size_t>> r(cur.size());
       for (size_t s = 0; s < cur.size(); ++s) {
         int32_t dummy = -1;
@@ -280,7 +283,7 @@ int plan_kernelize(PlanImpl* p) {
       cur.swap(keep);
     }
     std::unordered_map<uint64_t, std::vector<size_t>> index;
-    std::vector<State> next;
+    std::vector<State> next, staged;
     auto offer = [&](State&& s) {
       std::sort(s.ks.begin(), s.ks.end());
       uint64_t h = hash_state(s.ks);
@@ -301,7 +304,7 @@ int plan_kernelize(PlanImpl* p) {
       int sub = -1;
       for (size_t k = 0; k < st.ks.size(); ++k) {
         const OpenK& K = st.ks[k];
-        if (((u.q & ~K.q) == 0 || (K.q & ~u.q) == 0) && admits(c, K, u)) {
+        if (((u.st.q & ~K.q) == 0 || (K.q & ~u.st.q) == 0) && admits(c, K, u)) {
           sub = (int)k;
           break;
         }
@@ -322,16 +325,16 @@ int plan_kernelize(PlanImpl* p) {
         int tgt;
         if (cand >= 0) {
           OpenK& K = ns.ks[cand];
-          K.q |= u.q;
-          K.ni |= u.ni;
-          K.gcost += u.gcost;
+          K.q |= u.st.q;
+          K.ni |= u.st.ni;
+          K.st.merge(u.st);
           tgt = cand;
         } else {
           OpenK K;
           K.fusion = cand == -2;
-          K.q = u.q;
-          K.ni = u.ni;
-          K.gcost = u.gcost;
+          K.q = u.st.q;
+          K.ni = u.st.ni;
+          K.st = u.st;
           if (!c.fits(K)) continue;
           K.id = c.new_id(K.fusion);
           ns.ks.push_back(K);
@@ -345,9 +348,9 @@ int plan_kernelize(PlanImpl* p) {
           if ((int)k == tgt) continue;
           OpenK& K = ns.ks[k];
           if (K.ext == ALLQ) {
-            if (conflict(u.q, u.ni, K.q, K.ni)) restrict_now.push_back((int)k);
+            if (conflict(u.st.q, u.st.ni, K.q, K.ni)) restrict_now.push_back((int)k);
           } else {
-            K.ext &= ~u.q;
+            K.ext &= ~u.st.q;
           }
         }
         // expand the merge choices kernel by kernel
@@ -359,7 +362,7 @@ int plan_kernelize(PlanImpl* p) {
             {
               State r = b;
               OpenK& K = r.ks[rk];
-              K.ext = K.q & ~u.q;
+              K.ext = K.q & ~u.st.q;
               out.push_back(std::move(r));
             }
             // option 2: merge with an all-extensible kernel
@@ -375,13 +378,13 @@ int plan_kernelize(PlanImpl* p) {
               OpenK m = B;
               m.q |= A.q;
               m.ni |= A.ni;
-              m.gcost += A.gcost;
+              m.st.merge(A.st);
               if (!c.fits(m)) continue;
               State r = b;
               r.pend.push_back(Event{1, A.id, B.id, -1});
-              if ((int)o != tgt && !conflict(u.q, u.ni, B.q, B.ni)) {
+              if ((int)o != tgt && !conflict(u.st.q, u.st.ni, B.q, B.ni)) {
                 // the merged kernel is restricted by u through A's qubits
-                m.ext = m.q & ~u.q;
+                m.ext = m.q & ~u.st.q;
               }
               r.ks[o] = m;
               r.ks[rk].id = -2;  // removed below
@@ -393,22 +396,32 @@ int plan_kernelize(PlanImpl* p) {
         for (State& b : branch) {
           b.ks.erase(std::remove_if(b.ks.begin(), b.ks.end(), [](const OpenK& k) { return k.id == -2; }),
                      b.ks.end());
-          // close kernels that can no longer grow
-          double open = 0;
-          std::vector<OpenK> keep;
-          for (const OpenK& K : b.ks) {
-            bool dead = K.ext == 0;
-            if (dead) b.closed += c.kcost(K);
-            else {
-              keep.push_back(K);
-              open += c.kcost(K);
-            }
-          }
-          b.ks.swap(keep);
-          b.open_cost = open;
-          offer(std::move(b));
+          staged.push_back(std::move(b));
         }
       }
+    }
+    // costs of every successor's kernels (one batch for a learned model),
+    // then close the kernels that can no longer grow and keep the best state
+    // per open-kernel set
+    if (c.cm.learned) {
+      std::vector<std::pair<KStat, bool>> want;
+      for (const State& b : staged)
+        for (const OpenK& K : b.ks) want.push_back({K.st, K.fusion != 0});
+      c.cm.prefetch(want);
+    }
+    for (State& b : staged) {
+      double open = 0;
+      std::vector<OpenK> keep;
+      for (const OpenK& K : b.ks) {
+        if (K.ext == 0) b.closed += c.kcost(K);
+        else {
+          keep.push_back(K);
+          open += c.kcost(K);
+        }
+      }
+      b.ks.swap(keep);
+      b.open_cost = open;
+      offer(std::move(b));
     }
     if (next.empty()) return QS_EPLAN;  // no feasible kernel for this gate
     for (State& s2 : next) {
@@ -515,14 +528,10 @@ int plan_kernelize(PlanImpl* p) {
   // finish kernels in the DP's chosen type
   for (int a : order) {
     Kernel k = std::move(ks[a]);
-    uint64_t qm = 0, nim = 0;
-    double gs = 0;
-    for (int g : k.gates) {
-      qm |= p->gates[g].qmask;
-      nim |= p->gates[g].nimask;
-      gs += c.cm.gate_cost(p->gates[g].type);
-    }
-    double cf = c.cm.fusion(qm), csh = c.cm.shm(nim, gs);
+    KStat s;
+    for (int g : k.gates) s.add(p->gates[g], c.cm.gate_cost(p->gates[g].type));
+    const uint64_t qm = s.q, nim = s.ni;
+    double cf = c.cm.fusion(s), csh = c.cm.shm(s);
     if (k.type == QS_KERNEL_FUSED && cf == INF) k.type = QS_KERNEL_SHM;
     if (k.type == QS_KERNEL_SHM && csh == INF) k.type = QS_KERNEL_FUSED;
     if (k.type == QS_KERNEL_SHM) {

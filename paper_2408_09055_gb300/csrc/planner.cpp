@@ -29,40 +29,46 @@ static uint64_t low_mask(int k, int n) {
   return b <= 0 ? 0ull : (b >= 64 ? ~0ull : ((1ull << b) - 1));
 }
 
-double CostModel::fusion(uint64_t qmask) const {
+double CostModel::fusion(const KStat& s) const {
   const auto& o = plan->opts;
-  int k = popc(qmask);
+  int k = popc(s.q);
   if (o.fuse_kmax <= 0 || k > o.fuse_kmax) return INF;
+  if (learned) return learned_cost(learned, s, true);
   int ke = std::max(k, std::min(o.fuse_kmin, plan->n));  // widened to fuse_kmin
   return plan->cost.fuse_cost[ke];
 }
 
-double CostModel::shm(uint64_t nimask, double gate_cost_sum) const {
+double CostModel::shm(const KStat& s) const {
   const auto& o = plan->opts;
-  uint64_t a = nimask | low_mask(o.forced_low, plan->n);
+  uint64_t a = s.ni | low_mask(o.forced_low, plan->n);
   if (popc(a) > o.shm_max_active) return INF;
-  return plan->cost.alpha + gate_cost_sum;
+  if (learned) return learned_cost(learned, s, false);
+  return plan->cost.alpha + s.gcost;
+}
+
+void CostModel::prefetch(const std::vector<std::pair<KStat, bool>>& ks) const {
+  if (learned) learned_prefetch(learned, ks);
+}
+
+static KStat stat_of(const PlanImpl* p, const std::vector<int32_t>& gates) {
+  KStat s;
+  for (int g : gates) s.add(p->gates[g], p->cost.gate_cost[p->gates[g].type]);
+  return s;
 }
 
 // Chooses the cheaper feasible type for a finished kernel (ties: shm).
 static bool finish_kernel(const PlanImpl* p, Kernel* k) {
-  CostModel cm{p};
-  uint64_t qm = 0, nim = 0;
-  double gs = 0;
-  for (int g : k->gates) {
-    qm |= p->gates[g].qmask;
-    nim |= p->gates[g].nimask;
-    gs += cm.gate_cost(p->gates[g].type);
-  }
-  double cf = cm.fusion(qm), cs = cm.shm(nim, gs);
+  CostModel cm{p, p->learned};
+  const KStat s = stat_of(p, k->gates);
+  double cf = cm.fusion(s), cs = cm.shm(s);
   if (cf == INF && cs == INF) return false;
   if (cs <= cf) {
     k->type = QS_KERNEL_SHM;
-    k->mask = nim | low_mask(p->opts.forced_low, p->n);
+    k->mask = s.ni | low_mask(p->opts.forced_low, p->n);
     k->cost = cs;
   } else {
     k->type = QS_KERNEL_FUSED;
-    k->mask = qm;
+    k->mask = s.q;
     k->cost = cf;
   }
   return true;
@@ -105,19 +111,31 @@ static int plan_greedy(PlanImpl* p) {
 
 static int plan_ordered(PlanImpl* p) {
   const size_t L = p->gates.size();
-  CostModel cm{p};
+  CostModel cm{p, p->learned};
   std::vector<double> dp(L + 1, INF);
   std::vector<int64_t> from(L + 1, -1);
   dp[0] = 0;
+  const uint64_t low = low_mask(p->opts.forced_low, p->n);
+  std::vector<std::pair<KStat, bool>> want;
   for (size_t i = 0; i < L; ++i) {
-    uint64_t qm = 0, nim = 0;
-    double gs = 0;
+    if (cm.learned) {  // batch every segment ending at i
+      want.clear();
+      KStat s;
+      for (int64_t j = (int64_t)i; j >= 0; --j) {
+        s.add(p->gates[j], 0.0);
+        const bool fok = p->opts.fuse_kmax > 0 && popc(s.q) <= p->opts.fuse_kmax;
+        const bool sok = popc(s.ni | low) <= p->opts.shm_max_active;
+        if (!fok && !sok) break;
+        if (fok) want.push_back({s, true});
+        if (sok) want.push_back({s, false});
+      }
+      cm.prefetch(want);
+    }
+    KStat s;
     for (int64_t j = (int64_t)i; j >= 0; --j) {
       const Gate& g = p->gates[j];
-      qm |= g.qmask;
-      nim |= g.nimask;
-      gs += cm.gate_cost(g.type);
-      double c = std::min(cm.fusion(qm), cm.shm(nim, gs));
+      s.add(g, cm.gate_cost(g.type));
+      double c = std::min(cm.fusion(s), cm.shm(s));
       if (c == INF) break;  // feasibility only shrinks as the segment grows
       double cand = dp[j] + c;
       if (cand < dp[i + 1]) {
@@ -143,14 +161,22 @@ int plan_kernelize(PlanImpl* p);  // kernelize.cpp
 int plan_kernels(PlanImpl* p) {
   p->kernels.clear();
   if (p->gates.empty()) return QS_OK;
+  if (p->opts.cost_kind == QS_COST_LEARNED) {
+    int st = QS_OK;
+    p->learned = learned_create(p, const_cast<qs_mlp*>(p->opts.mlp), &st);
+    if (!p->learned) return st;
+  }
   int rc;
   switch (p->opts.algo) {
     case QS_ALGO_PER_GATE: rc = plan_per_gate(p); break;
     case QS_ALGO_GREEDY: rc = plan_greedy(p); break;
     case QS_ALGO_ORDERED: rc = plan_ordered(p); break;
     case QS_ALGO_KERNELIZE: rc = plan_kernelize(p); break;
-    default: return QS_EINVAL;
+    default: rc = QS_EINVAL; break;
   }
+  if (rc == QS_OK) rc = learned_status(p->learned);  // a failed inference call
+  learned_destroy(p->learned);
+  p->learned = nullptr;
   if (rc != QS_OK) return rc;
   p->total_cost = 0;
   for (auto& k : p->kernels) p->total_cost += k.cost;
@@ -325,15 +351,11 @@ static bool compile_shm(const PlanImpl* p, const Kernel& K, ShmProgram* sp) {
   return true;
 }
 
-// Widens a shared-memory kernel's active set with the lowest inactive qubits
-// so that every tile is at least 2^10 amplitudes (coalescing and occupancy;
-// extra active qubits do not change the result).
-static uint64_t widen_active(uint64_t mask, int n, int want) {
-  for (int q = 0; q < n && std::popcount(mask) < want; ++q) mask |= 1ull << q;
-  return mask;
-}
-
-static uint64_t widen_fused(uint64_t mask, int n, int want) {
+// Widens a kernel's qubit set with the lowest unused qubits up to `want`
+// qubits (shared-memory tiles of at least 2^10 amplitudes for coalescing and
+// occupancy; fused kernels up to their minimum width).  Extra qubits do not
+// change the result.
+uint64_t widen_mask(uint64_t mask, int n, int want) {
   for (int q = 0; q < n && std::popcount(mask) < want; ++q) mask |= 1ull << q;
   return mask;
 }
@@ -347,7 +369,7 @@ int compile_programs(PlanImpl* p) {
     Kernel& k = p->kernels[i];
     if (k.type == QS_KERNEL_SHM) {
       int want = std::min(p->n, std::max(std::min(10, kMaxShmActive), std::popcount(k.mask)));
-      k.mask = widen_active(k.mask, p->n, want);
+      k.mask = widen_mask(k.mask, p->n, want);
       if (std::popcount(k.mask) > kMaxShmActive) return QS_EPLAN;
       if (!compile_shm(p, k, &p->shm[i])) return QS_EPLAN;
       if (p->opts.shm_variant != 1 && p->shm[i].m >= kMinPhasedM)
@@ -357,7 +379,7 @@ int compile_programs(PlanImpl* p) {
       const bool tc = p->opts.precision != QS_PREC_FP32;
       int kmin = tc ? std::max(p->opts.fuse_kmin, kTcTargets) : p->opts.fuse_kmin;
       int want = std::min(p->n, std::max(kmin, std::popcount(k.mask)));
-      k.mask = widen_fused(k.mask, p->n, want);
+      k.mask = widen_mask(k.mask, p->n, want);
       if (std::popcount(k.mask) > kMaxFuse) return QS_EPLAN;
       compile_fused(p, k, &p->fused[i]);
       if (tc) {

@@ -20,6 +20,7 @@ QS_ALGO_PER_GATE, QS_ALGO_GREEDY, QS_ALGO_ORDERED, QS_ALGO_KERNELIZE = 0, 1, 2, 
 QS_COST_ANALYTIC, QS_COST_LEARNED = 0, 1
 QS_PREC_FP32, QS_PREC_TF32, QS_PREC_TF32X3 = 0, 1, 2
 QS_KERNEL_SHM, QS_KERNEL_FUSED = 0, 1
+QS_MLP_FEATURES = 44
 NUM_GATE_TYPES = 10
 
 
@@ -109,6 +110,16 @@ def _load():
         "qs_remap": ([vp, vp, i32, ip, vp], ctypes.c_int),
         "qs_apply_fused": ([vp, i32, ip, i32, fp, i32, vp], ctypes.c_int),
         "qs_apply_fused_static": ([vp, i32, ip, i32, fp, i32, vp], ctypes.c_int),
+        "qs_mlp_create": ([i32, i32, u64, ctypes.POINTER(vp)], ctypes.c_int),
+        "qs_mlp_free": ([vp], None),
+        "qs_mlp_num_params": ([vp], i64),
+        "qs_mlp_shape": ([vp, ip, ip], ctypes.c_int),
+        "qs_mlp_get_params": ([vp, fp, u64], ctypes.c_int),
+        "qs_mlp_set_params": ([vp, fp, u64], ctypes.c_int),
+        "qs_mlp_gradient": ([vp, vp, vp, i32, fp, fp, vp], ctypes.c_int),
+        "qs_mlp_train_step": ([vp, vp, vp, i32, ctypes.c_float, fp, vp], ctypes.c_int),
+        "qs_mlp_forward": ([vp, vp, i32, vp, i32, vp], ctypes.c_int),
+        "qs_kernel_features": ([i32, vp, u64, i32, u64, fp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -148,11 +159,14 @@ def default_opts(**kw) -> qs_plan_opts:
     o = qs_plan_opts()
     _lib.qs_plan_opts_default(ctypes.byref(o))
     for k, v in kw.items():
-        if k == "cost":
+        if k in ("cost", "mlp"):
             continue
         setattr(o, k, v)
     if kw.get("cost") is not None:
         o.cost = ctypes.pointer(kw["cost"])
+    if kw.get("mlp") is not None:
+        o.mlp = kw["mlp"].h.value
+        o.cost_kind = QS_COST_LEARNED
     return o
 
 
@@ -318,3 +332,60 @@ def qs_apply_fused_static(state_ptr: int, n: int, targets, u: np.ndarray, precis
     check(_lib.qs_apply_fused_static(state_ptr, n, t, len(targets),
                                      uu.view(np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                      precision, _stream_ptr(stream)), "qs_apply_fused_static")
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Mlp:
+    """Owns a ``qs_mlp*`` (learned kernel-cost model, device parameters)."""
+
+    def __init__(self, features: int = QS_MLP_FEATURES, hidden: int = 128, seed: int = 0):
+        h = ctypes.c_void_p()
+        check(_lib.qs_mlp_create(int(features), int(hidden), int(seed), ctypes.byref(h)), "qs_mlp_create")
+        self.h = h
+        self.features, self.hidden = features, hidden
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.qs_mlp_free(self.h)
+            self.h = None
+
+    @property
+    def num_params(self) -> int:
+        return int(_lib.qs_mlp_num_params(self.h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        check(_lib.qs_mlp_get_params(self.h, _fp(out), out.size), "qs_mlp_get_params")
+        return out
+
+    def set_params(self, theta) -> None:
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        check(_lib.qs_mlp_set_params(self.h, _fp(t), t.size), "qs_mlp_set_params")
+
+    def gradient(self, x_ptr: int, t_ptr: int, batch: int, stream=None):
+        g = np.empty(self.num_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        check(_lib.qs_mlp_gradient(self.h, x_ptr, t_ptr, int(batch), _fp(g), _fp(loss), _stream_ptr(stream)),
+              "qs_mlp_gradient")
+        return float(loss[0]), g
+
+    def train_step(self, x_ptr: int, t_ptr: int, batch: int, lr: float, stream=None) -> float:
+        loss = np.zeros(1, dtype=np.float32)
+        check(_lib.qs_mlp_train_step(self.h, x_ptr, t_ptr, int(batch), float(lr), _fp(loss),
+                                     _stream_ptr(stream)), "qs_mlp_train_step")
+        return float(loss[0])
+
+    def forward(self, x_ptr: int, batch: int, y_ptr: int, bf16: bool, stream=None) -> None:
+        check(_lib.qs_mlp_forward(self.h, x_ptr, int(batch), y_ptr, 1 if bf16 else 0, _stream_ptr(stream)),
+              "qs_mlp_forward")
+
+
+def qs_kernel_features(n: int, gates, kernel_type: int, qubit_mask: int) -> np.ndarray:
+    g = _gates_array(gates)
+    out = np.zeros(QS_MLP_FEATURES, dtype=np.float32)
+    check(_lib.qs_kernel_features(int(n), g.ctypes.data_as(ctypes.c_void_p), len(g), int(kernel_type),
+                                  int(qubit_mask), _fp(out)), "qs_kernel_features")
+    return out

@@ -1,0 +1,114 @@
+"""The learned cost model's CUDA kernels against the FP64 oracle
+(oracle/mlp.py), BF16 inference against FP32, and learned-cost planning."""
+import numpy as np
+import pytest
+
+from oracle import mlp as OM
+from oracle import plan as OP
+from oracle import sim
+from synth import circuits as C
+from tests.gpu_util import assert_close_state, need_gpu, run_plan_on_gpu, torch
+
+pytestmark = pytest.mark.gpu
+F = 44
+
+
+def _data(B, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    x = (rng.uniform(0, 1, size=(B, F)) * scale).astype(np.float32)
+    t = rng.normal(2.0, 1.0, size=B).astype(np.float32)
+    return x, t
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("H", [16, 128])
+def test_gradient_and_forward_match_oracle(H):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    net = Q.Mlp(F, H, seed=3)
+    theta = net.get_params().astype(np.float64)
+    x, t = _data(300, H)
+    xd, td = _dev(x), _dev(t)
+    loss, g = net.gradient(xd.data_ptr(), td.data_ptr(), len(t))
+    ref_loss, ref_g = OM.gradient(theta, x.astype(np.float64), t.astype(np.float64), F, H)
+    assert abs(loss - ref_loss) <= 1e-4 * max(1.0, ref_loss)
+    assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
+    y = torch.empty(len(t), dtype=torch.float32, device="cuda")
+    net.forward(xd.data_ptr(), len(t), y.data_ptr(), bf16=False)
+    ref_y, _ = OM.forward(theta, x.astype(np.float64), F, H)
+    assert np.max(np.abs(y.cpu().numpy() - ref_y)) <= 1e-4 * max(1.0, np.max(np.abs(ref_y)))
+
+
+def test_bf16_inference_close_to_fp32():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    net = Q.Mlp(F, 128, seed=5)
+    x, _ = _data(512, 9)
+    xd = _dev(x)
+    y32 = torch.empty(512, dtype=torch.float32, device="cuda")
+    y16 = torch.empty(512, dtype=torch.float32, device="cuda")
+    net.forward(xd.data_ptr(), 512, y32.data_ptr(), bf16=False)
+    net.forward(xd.data_ptr(), 512, y16.data_ptr(), bf16=True)
+    a, b = y32.cpu().numpy(), y16.cpu().numpy()
+    assert np.max(np.abs(a - b) / (np.abs(a) + 1.0)) < 1e-2
+
+
+def test_train_step_is_one_adam_step():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    H = 32
+    net = Q.Mlp(F, H, seed=11)
+    theta = net.get_params().astype(np.float64)
+    x, t = _data(128, 4)
+    net.train_step(_dev(x).data_ptr(), _dev(t).data_ptr(), 128, 1e-3)
+    _, g = OM.gradient(theta, x.astype(np.float64), t.astype(np.float64), F, H)
+    ref = OM.Adam(theta.size, lr=1e-3).step(theta, g)
+    got = net.get_params()
+    # the first step moves each parameter by ~lr * sign(g); compare the moves
+    assert np.allclose(got - theta, ref - theta, atol=2e-6)
+
+
+def test_training_reduces_loss():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    net = Q.Mlp(F, 64, seed=1)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0, 1, size=(1024, F)).astype(np.float32)
+    t = (3.0 * x[:, 0] - 2.0 * x[:, 5] + np.sin(4 * x[:, 7])).astype(np.float32)
+    xd, td = _dev(x), _dev(t)
+    l0, _ = net.gradient(xd.data_ptr(), td.data_ptr(), 1024)
+    for _ in range(400):
+        net.train_step(xd.data_ptr(), td.data_ptr(), 1024, 3e-3)
+    l1, _ = net.gradient(xd.data_ptr(), td.data_ptr(), 1024)
+    assert l1 < 0.05 * l0
+
+
+@pytest.mark.parametrize("algo", [2, 3])
+def test_learned_cost_plans_are_valid_and_correct(algo):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 14
+    g = C.mixed_circuit(n, 300, 8)
+    net = Q.Mlp(F, 64, seed=2)
+    theta = net.get_params()
+    theta[-1] = 7.0  # about 1 ms per kernel
+    net.set_params(theta)
+    plan = Q.Plan(n, g, algo=algo, mlp=net, fuse_kmax=6, precision=Q.QS_PREC_TF32X3)
+    assert plan.opts.cost_kind == Q.QS_COST_LEARNED
+    assert plan.validate() == 0
+    OP.check_plan(g, plan.kernels())
+    got, _, _ = run_plan_on_gpu(n, plan)
+    assert_close_state(got, sim.apply(n, g))
+
+
+def test_timing_generator_and_training_end_to_end():
+    need_gpu()
+    from paper_2408_09055_gb300 import costmodel as CM
+    X, y, meta = CM.generate(n=18, count=48, seed=1, reps=2, batch=16, log=None)
+    assert X.shape == (meta["count"], F) and meta["count"] >= 40
+    assert np.all(np.isfinite(y))
+    net, metrics = CM.train(X, y, hidden=32, epochs=20, batch=16)
+    assert np.isfinite(metrics["train"]["mse"])
