@@ -207,6 +207,17 @@ def make_plan(Q, gates, which, shm_max=13, algo=None):
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=prec, fuse_kmax=6, fuse_kmin=6,
                               cost=cost)
         return Q.Plan(N_QUBITS, gates, opts), f"{which}: Kernelize, every kernel a fused 2^6 unitary"
+    if which == "B":  # learned-cost Kernelize, fused kernels on tensor cores in 3xTF32
+        from paper_2408_09055_gb300 import costmodel as CM
+        net, meta = CM.load()
+        opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3,
+                              shm_max_active=shm_max, fuse_kmax=6, mlp=net)
+        if algo == "ordered":
+            opts.algo = Q.QS_ALGO_ORDERED
+        plan = Q.Plan(N_QUBITS, gates, opts)
+        plan._net = net  # the model must outlive planning only, kept for reference
+        return plan, ("B: learned-cost Kernelize (MLP trained on this GPU's kernel timings), "
+                      "shared-memory kernels + fused 3xTF32 tensor-core kernels")
     if which == "A" and algo == "ordered":
         opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, cost_kind=Q.QS_COST_ANALYTIC,
                               precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0)

@@ -173,3 +173,26 @@ def load(path=MODEL_PATH):
     net = Q.Mlp(int(d["features"]), int(d["hidden"]))
     net.set_params(d["theta"])
     return net, json.loads(str(d["meta"]))
+
+
+def main(argv=None):
+    """python -m paper_2408_09055_gb300.costmodel [--count N] [--out PATH]:
+    times `count` kernels on a 30-qubit state, trains, saves the model and the
+    dataset beside it."""
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--out", default=MODEL_PATH)
+    a = ap.parse_args(argv)
+    X, y, meta = generate(count=a.count, seed=a.seed)
+    np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, meta=json.dumps(meta))
+    net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print)
+    meta["metrics"] = metrics
+    save(net, a.out, meta)
+    print(json.dumps(meta))
+
+
+if __name__ == "__main__":
+    main()
