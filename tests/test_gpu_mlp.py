@@ -67,7 +67,10 @@ def test_bf16_inference_matches_its_definition_and_fp32():
     h1 = _bf16(np.maximum(_bf16(x) @ _bf16(p["W1"]) + _bf16(p["b1"]), 0))
     h2 = _bf16(np.maximum(h1 @ _bf16(p["W2"]) + _bf16(p["b2"]), 0))
     emu = h2 @ _bf16(p["W3"]) + _bf16(p["b3"])[0]
-    assert np.max(np.abs(b - emu) / (np.abs(emu) + 1.0)) < 1e-5
+    # FP32 accumulation can flip a hidden activation to the neighbouring BF16
+    # value (one unit in 2^8); the output moves by far less than that
+    d = np.abs(b - emu) / (np.abs(emu) + 1.0)
+    assert np.max(d) < 2e-3 and np.mean(d) < 1e-4
     gap = np.abs(a - b) / (np.abs(a) + 1.0)
     assert np.mean(gap) < 5e-3 and np.max(gap) < 3e-2
 
@@ -79,12 +82,22 @@ def test_train_step_is_one_adam_step():
     net = Q.Mlp(F, H, seed=11)
     theta = net.get_params().astype(np.float64)
     x, t = _data(128, 4)
-    net.train_step(_dev(x).data_ptr(), _dev(t).data_ptr(), 128, 1e-3)
-    _, g = OM.gradient(theta, x.astype(np.float64), t.astype(np.float64), F, H)
-    ref = OM.Adam(theta.size, lr=1e-3).step(theta, g)
+    xd, td = _dev(x), _dev(t)
+    # Adam applied to the library's own gradient (the gradient itself is
+    # checked against backprop above): near-zero components would otherwise
+    # step by +-lr on rounding noise
+    _, g = net.gradient(xd.data_ptr(), td.data_ptr(), 128)
+    opt = OM.Adam(theta.size, lr=1e-3)
+    ref = opt.step(theta, g.astype(np.float64))
+    net.train_step(xd.data_ptr(), td.data_ptr(), 128, 1e-3)
     got = net.get_params()
-    # the first step moves each parameter by ~lr * sign(g); compare the moves
-    assert np.allclose(got - theta, ref - theta, atol=2e-6)
+    assert np.allclose(got, ref, atol=2e-7, rtol=0)
+    # a second step with the second gradient
+    theta2 = got.astype(np.float64)
+    _, g2 = net.gradient(xd.data_ptr(), td.data_ptr(), 128)
+    ref2 = opt.step(theta2, g2.astype(np.float64))
+    net.train_step(xd.data_ptr(), td.data_ptr(), 128, 1e-3)
+    assert np.allclose(net.get_params(), ref2, atol=4e-7, rtol=0)
 
 
 def test_training_reduces_loss():
