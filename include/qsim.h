@@ -104,7 +104,13 @@ typedef struct qs_plan_opts {
   int32_t fuse_kmax;      /* widest fused kernel; 0 disables fusion            */
   int32_t prune_T;        /* Kernelize pruning threshold T (<= 0: no pruning)  */
   int32_t attach_single;  /* Kernelize: attach one-qubit gates to neighbours   */
-  int32_t local_qubits;   /* L: qubits resident on the GPU per chunk (0 = n)   */
+  int32_t local_qubits;   /* L: qubits resident on the GPU per chunk (0 or >= n:
+                             no staging).  With 12 <= L < n the circuit is
+                             staged (Alg. 1's Stage, Sec. 4): each stage holds
+                             L local qubits, containing every non-insular
+                             qubit of its gates, and runs chunk by chunk
+                             through qs_run_plan_host.  L must also be >=
+                             shm_max_active and >= forced_low + 2.          */
   int32_t shm_variant;    /* shared-memory kernel: 0 auto (specialised if it
                              compiles, else interpreted, else generic),
                              1 generic tile kernel, 2 register-phased
@@ -172,6 +178,16 @@ int64_t qs_plan_kernel_source(const qs_plan* plan, uint64_t k, char* out, uint64
  * QS_OK or QS_EPLAN.                                                        */
 int qs_plan_validate(const qs_plan* plan, const qs_gate* gates, uint64_t ngates);
 
+/* Stage `stage` of a plan (0..num_stages-1; an unstaged plan has one stage
+ * holding every qubit): the mask of its local qubits, its gate count and
+ * the range [first_kernel, first_kernel + num_kernels) of its kernels in the
+ * plan's kernel list (kernels are listed stage by stage).  Staged plans
+ * (Sec. 4): a stage's gates have all their non-insular qubits local; its
+ * kernels' qubit masks are logical qubits inside the local set.  Outputs
+ * may be NULL.                                                              */
+int qs_plan_stage(const qs_plan* plan, int32_t stage, uint64_t* local_mask, int64_t* num_gates,
+                  int32_t* first_kernel, int32_t* num_kernels);
+
 /* ---- state ---------------------------------------------------------------- */
 typedef struct qs_state qs_state;
 
@@ -190,6 +206,29 @@ int qs_state_set_zero(qs_state* st, void* stream); /* |0...0> */
  * found asynchronously surface at the next synchronising call.             */
 int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream);
 
+/* Alg. 1's Execute with the state in host memory: for each stage, for each
+ * chunk of 2^L amplitudes that share one value of the stage's regional
+ * qubits, copy the chunk to the GPU, run the stage's kernels on it (the
+ * regional values are known bits of insular gates, Definition 2) and copy
+ * it back.  Chunks are double or triple buffered over internal streams, so
+ * copies in both directions overlap the kernels of the neighbouring chunks;
+ * a stage starts after every chunk of the previous one is back.
+ *   host_state   2^n complex64 amplitudes (interleaved float pairs), updated
+ *                in place; page-locked (cudaMallocHost / cudaHostRegister),
+ *                16-byte aligned, else QS_EINVAL.  Caller-owned.
+ *   device_buffer, buffer_bytes
+ *                device scratch for min(3, buffer_bytes / (8 * 2^L)) chunk
+ *                buffers (>= 1, 256-byte aligned), caller-owned; NULL: the
+ *                library allocates two (one when L = n) stream-ordered for
+ *                the call.
+ * An unstaged plan runs as one stage with L = n (one copy each way).  The
+ * call is asynchronous: work is ordered after what `stream` has queued and
+ * `stream` continues after the last copy back; the host must not touch
+ * host_state until then.  Errors: QS_EINVAL, QS_ECUDA, QS_ENOMEM.  After a
+ * failure the host state is undefined.                                       */
+int qs_run_plan_host(const qs_plan* plan, float* host_state, void* device_buffer,
+                     uint64_t buffer_bytes, void* stream);
+
 /* Per-kernel timing with CUDA events on the launching stream (used by the
  * benchmark for the roofline of each kernel type).  A timer holds
  * (num_kernels + 1) * max_runs events; qs_run_plan_timed records one event
@@ -198,6 +237,7 @@ int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream);
  * plan, the sum over recorded runs of its duration in ms (per_kernel_ms
  * has num_kernels entries) and the number of runs.                          */
 typedef struct qs_timer qs_timer;
+/* (Staged plans have no resident form: QS_EUNSUPPORTED.) */
 int qs_timer_create(const qs_plan* plan, uint64_t max_runs, qs_timer** out);
 int qs_run_plan_timed(const qs_plan* plan, qs_state* st, qs_timer* timer, void* stream);
 int qs_timer_read(qs_timer* timer, double* per_kernel_ms, uint64_t cap, uint64_t* runs);

@@ -17,6 +17,10 @@
 * :func:`brute_force_any_order` -- the optimum over all topologically
   equivalent orders and all segmentations of them (tiny circuits).
 * :func:`extensible_by_definition` -- Definition 4 evaluated literally.
+* :func:`check_stages` -- a staged plan (Sec. 4): every stage has exactly L
+  local qubits, every gate of a stage has all its non-insular qubits local,
+  every kernel stays inside its stage's local qubits, and the concatenated
+  kernels form a valid plan of the whole circuit.
 """
 from __future__ import annotations
 
@@ -65,6 +69,24 @@ def check_plan(gates, kernels) -> None:
                 if must_precede(gates[i], gates[j]):
                     assert pos[i] < pos[j], f"gate {i} must precede gate {j}"
             last.setdefault(q, []).append(j)
+
+
+def check_stages(gates, stages, L) -> None:
+    """``stages``: list of (local qubit set, [(kernel type, kernel qubit set,
+    gate ids), ...]).  Kernel type 0 is shared-memory (its qubit set is the
+    active set), 1 is fused (its qubit set is the fused targets)."""
+    flat = []
+    for local, kernels in stages:
+        local = frozenset(local)
+        assert len(local) == L, "a stage holds exactly L local qubits"
+        for ktype, kq, ids in kernels:
+            assert frozenset(kq) <= local, "kernel qubits are local"
+            for i in ids:
+                assert noninsular_qubits(gates[i]) <= local, f"gate {i}: non-insular qubit not local"
+                if ktype == 1:
+                    assert gate_qubits(gates[i]) <= frozenset(kq), f"gate {i} outside its fused kernel"
+            flat.append(list(ids))
+    check_plan(gates, flat)
 
 
 class CostModel:

@@ -170,6 +170,107 @@ void qs_plan_opts_default(qs_plan_opts* o) {
   o->mlp = nullptr;
 }
 
+}  // extern "C"
+
+namespace qs {
+
+// Plans `count` gates (given by index into `gates`, relabelled through `pos`
+// when it is set) into P: Kernelize/Ordered, program compilation, Theorem 2
+// check.
+static int build_impl(PlanImpl& P, int n, const qs_gate* gates, const int32_t* ids,
+                      const int32_t* pos, uint64_t count) {
+  P.gates.resize(count);
+  for (uint64_t i = 0; i < count; ++i) {
+    qs_gate x = gates[ids ? ids[i] : i];
+    if (pos) {
+      if (x.q[0] < 0 || x.q[0] >= n || (x.nq == 2 && (x.q[1] < 0 || x.q[1] >= n))) return QS_EINVAL;
+      x.q[0] = pos[x.q[0]];
+      if (x.nq == 2) x.q[1] = pos[x.q[1]];
+    }
+    int rc = make_gate(x, n, &P.gates[i]);
+    if (rc != QS_OK) return rc;
+  }
+  int rc = plan_kernels(&P);
+  if (rc == QS_OK) rc = compile_programs(&P);
+  if (rc == QS_OK) rc = validate_plan(&P);
+  return rc;
+}
+
+// Staged plan: stage the circuit, plan every stage on its relabelled qubits
+// and flatten the kernels (logical qubits, circuit gate indices) into p->impl.
+static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o) {
+  PlanImpl& P = p->impl;
+  const int n = P.n, L = o.local_qubits;
+  int rc = stage_circuit(P.gates, n, L, &p->stages);
+  if (rc != QS_OK) return rc;
+  for (size_t si = 0; si < p->stages.size(); ++si) {
+    Stage& st = p->stages[si];
+    st.plan = std::make_unique<PlanImpl>();
+    PlanImpl& S = *st.plan;
+    S.n = n;
+    S.opts = o;
+    S.opts.local_qubits = 0;
+    S.cost = P.cost;
+    S.exec_limit = (1ull << L) - 1;
+    rc = build_impl(S, n, gates, st.gates.data(), st.pos.data(), st.gates.size());
+    if (rc != QS_OK) return rc;
+    for (size_t k = 0; k < S.kernels.size(); ++k) {
+      Kernel K = S.kernels[k];
+      K.stage = (int32_t)si;
+      for (auto& g : K.gates) g = st.gates[g];
+      uint64_t m = 0;
+      for (int b = 0; b < n; ++b)
+        if ((K.mask >> b) & 1) m |= 1ull << st.order[b];
+      K.mask = m;
+      P.kernels.push_back(std::move(K));
+      p->kmap.push_back({(int32_t)si, (int32_t)k});
+    }
+    P.total_cost += S.total_cost;
+    P.dp_states += S.dp_states;
+    P.jit_ms += S.jit_ms;
+  }
+  return QS_OK;
+}
+
+// A staged plan's own invariants on top of Theorem 2 over the flattened
+// kernel list: each gate's non-insular qubits and each kernel's qubits are
+// local in its stage, and the stage's programs are those of its gates.
+static int validate_staged(const qs_plan* p) {
+  const PlanImpl& P = p->impl;
+  int rc = validate_plan(&P);
+  if (rc != QS_OK) return rc;
+  if (P.kernels.size() != p->kmap.size()) return QS_EPLAN;
+  int32_t last = 0;
+  for (size_t k = 0; k < P.kernels.size(); ++k) {
+    const Kernel& K = P.kernels[k];
+    const int32_t si = p->kmap[k].first;
+    if (si < last || si >= (int32_t)p->stages.size() || K.stage != si) return QS_EPLAN;
+    last = si;
+    const Stage& st = p->stages[si];
+    if (K.mask & ~st.local) return QS_EPLAN;
+    for (int32_t g : K.gates)
+      if (P.gates[g].nimask & ~st.local) return QS_EPLAN;
+  }
+  for (const Stage& st : p->stages)
+    if (std::popcount(st.local) != P.opts.local_qubits || !st.plan || validate_plan(st.plan.get()) != QS_OK)
+      return QS_EPLAN;
+  return QS_OK;
+}
+
+static void free_device(PlanImpl& P) {
+  for (auto& d : P.dev) {
+    cudaSetDevice(d.device);
+    if (d.buf) cudaFree(d.buf);
+    for (auto l : d.libs)
+      if (l) cudaLibraryUnload(l);
+  }
+  P.dev.clear();
+}
+
+}  // namespace qs
+
+extern "C" {
+
 int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_plan_opts* opts,
                     qs_plan** out) {
   if (!out) return QS_EINVAL;
@@ -186,6 +287,13 @@ int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_p
   if (o.cost_kind == QS_COST_LEARNED && !o.mlp) return QS_EINVAL;
   if (o.cost_kind != QS_COST_ANALYTIC && o.cost_kind != QS_COST_LEARNED) return QS_EINVAL;
   if (o.shm_variant < 0 || o.shm_variant > 3) return QS_EINVAL;
+  if (o.local_qubits < 0) return QS_EINVAL;
+  if (o.local_qubits >= n) o.local_qubits = 0;
+  const bool staged = o.local_qubits > 0;
+  // a chunk holds the widest kernel (a 2^14 tile, a widened fused kernel)
+  if (staged && (o.local_qubits < kMinLocalQubits || o.local_qubits < o.shm_max_active ||
+                 o.local_qubits < o.forced_low + 2))
+    return QS_EINVAL;
   if (o.precision != QS_PREC_FP32 && o.fuse_kmax > 0) {
     // tensor-core fused kernels are 2^6 wide: narrower kernels are widened
     if (o.fuse_kmax > kTcTargets || n < kTcTargets + 5) return QS_EUNSUPPORTED;
@@ -199,27 +307,26 @@ int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_p
   P.opts = o;
   if (o.cost) P.cost = *o.cost; else qs_cost_table_default(&P.cost);
   P.opts.cost = nullptr;
+  o.cost = &P.cost;
   try {
-    P.gates.resize(ngates);
-    for (uint64_t i = 0; i < ngates; ++i) {
-      int rc = make_gate(gates[i], n, &P.gates[i]);
-      if (rc != QS_OK) {
-        delete p;
-        return rc;
-      }
+    int rc = QS_OK;
+    if (!staged) {
+      rc = build_impl(P, n, gates, nullptr, nullptr, ngates);
+    } else {
+      P.gates.resize(ngates);
+      for (uint64_t i = 0; i < ngates && rc == QS_OK; ++i) rc = make_gate(gates[i], n, &P.gates[i]);
+      if (rc == QS_OK) rc = build_staged(p, gates, o);
+      if (rc == QS_OK) rc = validate_staged(p);
     }
-    int rc = plan_kernels(&P);
-    if (rc == QS_OK) rc = compile_programs(&P);
-    if (rc == QS_OK) rc = validate_plan(&P);
     if (rc != QS_OK) {
-      delete p;
+      qs_plan_free(p);
       return rc;
     }
   } catch (const std::bad_alloc&) {
-    delete p;
+    qs_plan_free(p);
     return QS_ENOMEM;
   } catch (...) {
-    delete p;
+    qs_plan_free(p);
     return QS_EPLAN;
   }
   P.planner_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -231,13 +338,14 @@ void qs_plan_free(qs_plan* p) {
   if (!p) return;
   int cur = -1;
   cudaGetDevice(&cur);
-  for (auto& d : p->impl.dev) {
-    cudaSetDevice(d.device);
-    if (d.buf) cudaFree(d.buf);
-    for (auto l : d.libs)
-      if (l) cudaLibraryUnload(l);
-  }
-  if (cur >= 0 && !p->impl.dev.empty()) cudaSetDevice(cur);
+  bool any = !p->impl.dev.empty();
+  free_device(p->impl);
+  for (auto& st : p->stages)
+    if (st.plan) {
+      any = any || !st.plan->dev.empty();
+      free_device(*st.plan);
+    }
+  if (cur >= 0 && any) cudaSetDevice(cur);
   delete p;
 }
 
@@ -246,19 +354,23 @@ int qs_plan_stats_get(const qs_plan* p, qs_plan_stats* s) {
   const PlanImpl& P = p->impl;
   std::memset(s, 0, sizeof(*s));
   s->n = P.n;
-  s->num_stages = 1;
+  s->num_stages = p->stages.empty() ? 1 : (int32_t)p->stages.size();
   s->num_gates = P.gates.size();
   s->num_kernels = P.kernels.size();
   for (const auto& k : P.kernels) (k.type == QS_KERNEL_SHM ? s->num_shm : s->num_fused)++;
   s->cost = P.total_cost;
   s->planner_ms = P.planner_ms;
   s->dp_states = P.dp_states;
-  for (const auto& pg : P.shm2)
-    if (pg.ok) {
-      s->num_phased++;
-      s->num_exchanges += (uint64_t)(pg.num_phases - 1);
-      if (pg.jit_module >= 0) s->num_jit++;
-    }
+  auto count = [&](const PlanImpl& Q) {
+    for (const auto& pg : Q.shm2)
+      if (pg.ok) {
+        s->num_phased++;
+        s->num_exchanges += (uint64_t)(pg.num_phases - 1);
+        if (pg.jit_module >= 0) s->num_jit++;
+      }
+  };
+  if (p->stages.empty()) count(P);
+  for (const auto& st : p->stages) count(*st.plan);
   s->jit_ms = P.jit_ms;
   return QS_OK;
 }
@@ -285,10 +397,25 @@ int64_t qs_plan_kernel_gates(const qs_plan* p, uint64_t k, int32_t* ids, uint64_
   return (int64_t)K.gates.size();
 }
 
+// The plan and kernel index that hold kernel k's programs.
+static const PlanImpl* program_of(const qs_plan* p, uint64_t k, uint64_t* local) {
+  if (p->stages.empty()) {
+    *local = k;
+    return &p->impl;
+  }
+  const auto& [si, lk] = p->kmap[k];
+  *local = (uint64_t)lk;
+  return p->stages[si].plan.get();
+}
+
 int qs_plan_fused_matrix(const qs_plan* p, uint64_t k, double* out, uint64_t cap) {
   if (!p || !out || k >= p->impl.kernels.size()) return QS_EINVAL;
   if (p->impl.kernels[k].type != QS_KERNEL_FUSED) return QS_EINVAL;
-  const auto& u = p->impl.fused[k].u64;
+  uint64_t lk = 0;
+  const PlanImpl* Q = program_of(p, k, &lk);
+  // positions of a stage's local qubits ascend with the logical qubits, so
+  // the matrix's target order is the same in both labellings
+  const auto& u = Q->fused[lk].u64;
   if (cap < u.size()) return QS_EINVAL;
   std::copy(u.begin(), u.end(), out);
   return QS_OK;
@@ -296,9 +423,11 @@ int qs_plan_fused_matrix(const qs_plan* p, uint64_t k, double* out, uint64_t cap
 
 int64_t qs_plan_kernel_source(const qs_plan* p, uint64_t k, char* out, uint64_t cap) {
   if (!p || k >= p->impl.kernels.size()) return QS_EINVAL;
-  if (k >= p->impl.shm2.size() || !p->impl.shm2[k].ok) return QS_EINVAL;
+  uint64_t lk = 0;
+  const PlanImpl* Q = program_of(p, k, &lk);
+  if (lk >= Q->shm2.size() || !Q->shm2[lk].ok) return QS_EINVAL;
   std::string src;
-  if (!jit_source(p->impl.shm2[k], p->impl.n, "qsk" + std::to_string(k), &src)) return QS_EINVAL;
+  if (!jit_source(Q->shm2[lk], Q->n, "qsk" + std::to_string(lk), &src)) return QS_EINVAL;
   if (out) {
     if (cap < src.size() + 1) return QS_EINVAL;
     std::memcpy(out, src.c_str(), src.size() + 1);
@@ -316,7 +445,26 @@ int qs_plan_validate(const qs_plan* p, const qs_gate* gates, uint64_t ngates) {
     const Gate& h = P.gates[i];
     if (g.type != h.type || g.q0 != h.q0 || g.q1 != h.q1) return QS_EPLAN;
   }
-  return validate_plan(&P);
+  return p->stages.empty() ? validate_plan(&P) : validate_staged(p);
+}
+
+int qs_plan_stage(const qs_plan* p, int32_t stage, uint64_t* local_mask, int64_t* num_gates,
+                  int32_t* first_kernel, int32_t* num_kernels) {
+  if (!p) return QS_EINVAL;
+  const int32_t ns = p->stages.empty() ? 1 : (int32_t)p->stages.size();
+  if (stage < 0 || stage >= ns) return QS_EINVAL;
+  const PlanImpl& P = p->impl;
+  int32_t first = -1, cnt = 0;
+  for (size_t k = 0; k < P.kernels.size(); ++k)
+    if (P.kernels[k].stage == stage) {
+      if (first < 0) first = (int32_t)k;
+      cnt++;
+    }
+  if (local_mask) *local_mask = p->stages.empty() ? (P.n >= 64 ? ~0ull : (1ull << P.n) - 1) : p->stages[stage].local;
+  if (num_gates) *num_gates = p->stages.empty() ? (int64_t)P.gates.size() : (int64_t)p->stages[stage].gates.size();
+  if (first_kernel) *first_kernel = first < 0 ? 0 : first;
+  if (num_kernels) *num_kernels = cnt;
+  return QS_OK;
 }
 
 int qs_state_create(int32_t n, void* device_ptr, qs_state** out) {
@@ -366,6 +514,7 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
 int qs_timer_create(const qs_plan* plan, uint64_t max_runs, qs_timer** out) {
   if (!plan || !out || max_runs == 0) return QS_EINVAL;
   *out = nullptr;
+  if (!plan->stages.empty()) return QS_EUNSUPPORTED;
   qs_timer* t = new (std::nothrow) qs_timer();
   if (!t) return QS_ENOMEM;
   t->plan = plan;
@@ -419,15 +568,16 @@ int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream) {
   return run_plan_impl(plan, st, stream, nullptr);
 }
 
-static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_timer* tm) {
-  if (!plan || !st) return QS_EINVAL;
-  PlanImpl* P = const_cast<PlanImpl*>(&plan->impl);
-  if (P->n != st->n) return QS_EINVAL;
-  DeviceCache* dc = nullptr;
-  int rc = ensure_device(P, &dc);
-  if (rc != QS_OK) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t* ev = tm ? &tm->ev[tm->runs * (P->kernels.size() + 1)] : nullptr;
+}  // extern "C"
+
+namespace qs {
+
+// Launches the kernels of P on psi, a view of 2^n_addr amplitudes whose
+// qubits above n_addr have the known values `hi` (chunked execution; for a
+// resident state n_addr = P.n and hi = 0).  ev: nk + 1 events or null.
+static int run_kernels(PlanImpl* P, DeviceCache* dc, float2* psi, int n_addr, uint64_t hi,
+                       cudaStream_t s, cudaEvent_t* ev) {
+  int rc = QS_OK;
   for (size_t i = 0; i < P->kernels.size(); ++i) {
     const Kernel& K = P->kernels[i];
     if (ev) {
@@ -436,11 +586,12 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
     }
     const uint8_t* base = static_cast<const uint8_t*>(dc->buf) + dc->op_off[i];
     if (K.type == QS_KERNEL_SHM && dc->jit_kernel[i]) {
-      rc = launch_jit(dc->jit_kernel[i], P->shm2[i], st->psi, P->n, s);
+      rc = launch_jit(dc->jit_kernel[i], P->shm2[i], psi, n_addr, hi, s);
     } else if (K.type == QS_KERNEL_SHM && P->shm2[i].ok) {
       ShmV2Launch a;
-      a.psi = st->psi;
-      a.n = P->n;
+      a.psi = psi;
+      a.hi = hi;
+      a.n = n_addr;
       a.amask = K.mask;
       a.prog = reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(dc->buf) + dc->prog_off[i]);
       a.pg = &P->shm2[i];
@@ -448,8 +599,9 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
     } else if (K.type == QS_KERNEL_SHM) {
       const ShmProgram& sp = P->shm[i];
       ShmLaunch a;
-      a.psi = st->psi;
-      a.n = P->n;
+      a.psi = psi;
+      a.hi = hi;
+      a.n = n_addr;
       a.m = sp.m;
       std::copy(sp.act, sp.act + kMaxShmActive, a.act);
       a.ops = reinterpret_cast<const DevOp*>(base);
@@ -458,8 +610,8 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
     } else {
       const FusedProgram& fp = P->fused[i];
       FusedLaunch a;
-      a.psi = st->psi;
-      a.n = P->n;
+      a.psi = psi;
+      a.n = n_addr;
       a.k = fp.k;
       std::copy(fp.targets, fp.targets + kMaxFuse, a.targets);
       a.u = reinterpret_cast<const float2*>(base);
@@ -471,9 +623,137 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
   if (ev) {
     cudaError_t e = cudaEventRecord(ev[P->kernels.size()], s);
     if (e != cudaSuccess) return cuda_status(e);
-    tm->runs++;
   }
   return QS_OK;
+}
+
+}  // namespace qs
+
+extern "C" {
+
+static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_timer* tm) {
+  if (!plan || !st) return QS_EINVAL;
+  if (!plan->stages.empty()) return QS_EUNSUPPORTED;  // staged plans run through qs_run_plan_host
+  PlanImpl* P = const_cast<PlanImpl*>(&plan->impl);
+  if (P->n != st->n) return QS_EINVAL;
+  DeviceCache* dc = nullptr;
+  int rc = ensure_device(P, &dc);
+  if (rc != QS_OK) return rc;
+  cudaEvent_t* ev = tm ? &tm->ev[tm->runs * (P->kernels.size() + 1)] : nullptr;
+  rc = run_kernels(P, dc, st->psi, P->n, 0, (cudaStream_t)stream, ev);
+  if (rc == QS_OK && ev) tm->runs++;
+  return rc;
+}
+
+// ---- host-resident state: Alg. 1's Execute with the shards in host memory ----
+
+int qs_run_plan_host(const qs_plan* plan, float* host_state, void* device_buffer,
+                     uint64_t buffer_bytes, void* stream) {
+  if (!plan || !host_state) return QS_EINVAL;
+  if (reinterpret_cast<uintptr_t>(host_state) & 15) return QS_EINVAL;
+  const PlanImpl& P = plan->impl;
+  const int n = P.n;
+  const bool staged = !plan->stages.empty();
+  const int L = staged ? P.opts.local_qubits : n;
+  const uint64_t chunk_bytes = sizeof(float2) << L;
+  // the state must be page-locked (cudaMallocHost / cudaHostRegister) for
+  // the copies to run asynchronously on the copy engines
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, host_state);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (at.type != cudaMemoryTypeHost) return QS_EINVAL;
+  int nbuf = 0;
+  float2* dbuf = static_cast<float2*>(device_buffer);
+  if (dbuf) {
+    if (reinterpret_cast<uintptr_t>(dbuf) & 255) return QS_EINVAL;
+    nbuf = (int)std::min<uint64_t>(kMaxChunkBuffers, buffer_bytes / chunk_bytes);
+    if (nbuf < 1) return QS_EINVAL;
+  }
+  // device programs of every stage, before any work is queued
+  std::vector<PlanImpl*> plans;
+  if (staged)
+    for (const auto& st : plan->stages) plans.push_back(st.plan.get());
+  else
+    plans.push_back(const_cast<PlanImpl*>(&P));
+  std::vector<DeviceCache*> dcs(plans.size(), nullptr);
+  for (size_t i = 0; i < plans.size(); ++i) {
+    int rc = ensure_device(plans[i], &dcs[i]);
+    if (rc != QS_OK) return rc;
+  }
+  const cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t ss[kMaxChunkBuffers] = {};
+  cudaEvent_t evs[kMaxChunkBuffers + 1] = {};
+  const int nchunks_log = n - L;
+  if (!dbuf) nbuf = nchunks_log == 0 ? 1 : std::min(kMaxChunkBuffers, 2);
+  int rc = QS_OK;
+  bool allocated = false;
+  auto fail = [&](cudaError_t err) {
+    if (rc == QS_OK && err != cudaSuccess) rc = cuda_status(err);
+    return rc != QS_OK;
+  };
+  for (int b = 0; b < nbuf && rc == QS_OK; ++b)
+    fail(cudaStreamCreateWithFlags(&ss[b], cudaStreamNonBlocking));
+  for (int b = 0; b <= nbuf && rc == QS_OK; ++b)
+    fail(cudaEventCreateWithFlags(&evs[b], cudaEventDisableTiming));
+  // the internal streams start after the caller's stream
+  if (rc == QS_OK && !fail(cudaEventRecord(evs[nbuf], user)))
+    for (int b = 0; b < nbuf && rc == QS_OK; ++b) fail(cudaStreamWaitEvent(ss[b], evs[nbuf], 0));
+  if (rc == QS_OK && !dbuf) {
+    void* mem = nullptr;
+    if (!fail(cudaMallocAsync(&mem, chunk_bytes * nbuf, ss[0]))) {
+      dbuf = static_cast<float2*>(mem);
+      allocated = true;
+      if (!fail(cudaEventRecord(evs[0], ss[0])))
+        for (int b = 1; b < nbuf && rc == QS_OK; ++b) fail(cudaStreamWaitEvent(ss[b], evs[0], 0));
+    }
+  }
+  float2* hs = reinterpret_cast<float2*>(host_state);
+  const uint64_t nch = 1ull << nchunks_log;
+  for (size_t si = 0; si < plans.size() && rc == QS_OK; ++si) {
+    const Stage* st = staged ? &plan->stages[si] : nullptr;
+    const int run_log = staged ? st->run_log : n;
+    const uint64_t run_amps = 1ull << run_log;
+    const uint64_t nruns = 1ull << (L - run_log);
+    // host index of the chunk's regional bits / of run r's local high bits
+    auto deposit = [&](uint64_t v, int from, int count) {
+      uint64_t x = 0;
+      for (int t = 0; t < count; ++t)
+        if ((v >> t) & 1) x |= 1ull << st->order[from + t];
+      return x;
+    };
+    for (uint64_t c = 0; c < nch && rc == QS_OK; ++c) {
+      const int b = (int)(c % (uint64_t)nbuf);
+      const cudaStream_t s = ss[b];
+      float2* d = dbuf + (uint64_t(b) << L);
+      const uint64_t hbase = staged ? deposit(c, L, n - L) : 0;
+      for (uint64_t r = 0; r < nruns && rc == QS_OK; ++r) {
+        const uint64_t h = hbase | (staged ? deposit(r, run_log, L - run_log) : 0);
+        fail(cudaMemcpyAsync(d + (r << run_log), hs + h, run_amps * sizeof(float2), cudaMemcpyHostToDevice, s));
+      }
+      if (rc == QS_OK) rc = run_kernels(plans[si], dcs[si], d, L, c << L, s, nullptr);
+      for (uint64_t r = 0; r < nruns && rc == QS_OK; ++r) {
+        const uint64_t h = hbase | (staged ? deposit(r, run_log, L - run_log) : 0);
+        fail(cudaMemcpyAsync(hs + h, d + (r << run_log), run_amps * sizeof(float2), cudaMemcpyDeviceToHost, s));
+      }
+    }
+    // a stage reads what every chunk of the previous stage wrote back
+    if (si + 1 < plans.size() && nbuf > 1) {
+      for (int b = 0; b < nbuf && rc == QS_OK; ++b) fail(cudaEventRecord(evs[b], ss[b]));
+      for (int b = 0; b < nbuf && rc == QS_OK; ++b)
+        for (int o = 0; o < nbuf && rc == QS_OK; ++o)
+          if (o != b) fail(cudaStreamWaitEvent(ss[b], evs[o], 0));
+    }
+  }
+  // join: the caller's stream continues after every chunk is back in host memory
+  for (int b = 1; b < nbuf; ++b)
+    if (ss[b] && evs[b] && cudaEventRecord(evs[b], ss[b]) == cudaSuccess) cudaStreamWaitEvent(ss[0], evs[b], 0);
+  if (allocated) cudaFreeAsync(dbuf, ss[0]);
+  if (ss[0] && evs[0] && cudaEventRecord(evs[0], ss[0]) == cudaSuccess) cudaStreamWaitEvent(user, evs[0], 0);
+  for (int b = 0; b < nbuf; ++b)
+    if (ss[b]) cudaStreamDestroy(ss[b]);
+  for (int b = 0; b <= nbuf; ++b)
+    if (evs[b]) cudaEventDestroy(evs[b]);
+  return rc;
 }
 
 static int copy_amps(void* dst, const void* src, uint64_t first, uint64_t count, int n,

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -96,6 +97,9 @@ struct PlanImpl {
   std::string jit_log;              // first NVRTC error log, if any
   double jit_ms = 0;
   double planner_ms = 0, total_cost = 0;
+  // qubits a kernel may execute on (shm active set, fused targets); a
+  // stage's plan keeps its kernels inside the chunk's local qubits
+  uint64_t exec_limit = ~0ull;
   LearnedCost* learned = nullptr;  // set while planning with QS_COST_LEARNED
   uint64_t dp_states = 0;
   std::mutex mu;
@@ -150,9 +154,33 @@ int plan_kernels(PlanImpl* p);         // fills p->kernels
 int compile_programs(PlanImpl* p);     // fills p->shm / p->fused
 int validate_plan(const PlanImpl* p);  // Theorem 2 check
 
+// ---- staging (stager.cpp) ---------------------------------------------------
+// One stage of a staged plan (Alg. 1, Partition/Execute): a set of gates whose
+// non-insular qubits are all in `local` (Sec. 4), executed chunk by chunk.
+// A chunk holds the 2^L amplitudes that share one value of the regional
+// (non-local) qubits; on the GPU its index bits are the local qubits in
+// ascending order, so the stage's gates are relabelled by `pos` and planned
+// as an n-qubit circuit whose kernels stay in positions < L, with the
+// chunk's regional bits known (positions L..n-1, ascending).
+struct Stage {
+  uint64_t local = 0;            // logical qubits held on the GPU
+  std::vector<int32_t> gates;    // circuit indices, execution order
+  std::vector<int32_t> pos;      // logical qubit -> position in the chunked view
+  std::vector<int32_t> order;    // position -> logical qubit (inverse of pos)
+  int run_log = 0;               // local qubits 0..run_log-1: contiguous host runs
+  std::unique_ptr<PlanImpl> plan;
+};
+// local qubits the stager may choose freely; the rest, L - kStageSlots
+// lowest qubits, stay local in every stage so host runs are 2^(L-8) long
+constexpr int kStageSlots = 8;
+constexpr int kMinLocalQubits = 12;
+constexpr int kMaxChunkBuffers = 3;  // copy-in / compute / copy-out in flight  // a chunk holds a 2^12 tile and a tensor-core kernel
+int stage_circuit(const std::vector<Gate>& gates, int n, int L, std::vector<Stage>* out);
+
 // ---- device side (kernels_*.cu) ----------------------------------------------
 struct ShmLaunch {
   float2* psi;
+  uint64_t hi = 0;  // known bits of qubits above n (chunked execution)
   int n, m;
   int act[kMaxShmActive];
   const DevOp* ops;
@@ -162,6 +190,7 @@ int launch_shm(const ShmLaunch& a, cudaStream_t s);
 
 struct ShmV2Launch {
   float2* psi;
+  uint64_t hi = 0;
   int n;
   uint64_t amask;
   const uint32_t* prog;      // device copy of pg->prog
@@ -172,7 +201,7 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
 void fold_global_phase(std::vector<ShmProgramV2>& progs);
 int jit_compile_plan(PlanImpl* p);                 // jit.cpp
 bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::string* out);
-int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, cudaStream_t s);
+int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, uint64_t hi, cudaStream_t s);
 
 struct FusedLaunch {
   float2* psi;
@@ -198,7 +227,9 @@ void set_cuda_error(const char* what, cudaError_t e);
 }  // namespace qs
 
 struct qs_plan {
-  qs::PlanImpl impl;
+  qs::PlanImpl impl;  // staged plans: the gates and the flattened kernel list
+  std::vector<qs::Stage> stages;  // empty unless local_qubits < n
+  std::vector<std::pair<int32_t, int32_t>> kmap;  // flattened kernel -> (stage, kernel)
 };
 struct qs_state {
   int n = 0;

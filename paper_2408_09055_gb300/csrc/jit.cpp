@@ -98,7 +98,7 @@ struct Gen {
 
   // value (0/1) of a qubit reference that is not a register slot
   std::string known(uint32_t ref) const {
-    if (ref & REF_GLOBAL) return "((unsigned)(base >> " + std::to_string(ref & 63u) + ") & 1u)";
+    if (ref & REF_GLOBAL) return "((unsigned)((base | hi) >> " + std::to_string(ref & 63u) + ") & 1u)";
     const PhaseMap& pm = pg.maps[phase];
     int b = (int)(ref & 31u);
     for (int k = 0; k < pm.nt; ++k)
@@ -328,7 +328,7 @@ bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::str
   }
   const int minb = 1 << (kMaxShmActive - m);
   o << "extern \"C\" __global__ void __launch_bounds__(" << (1 << nt) << ", " << minb << ")\n"
-    << name << "(float2* __restrict__ psi, unsigned long long nb) {\n"
+    << name << "(float2* __restrict__ psi, unsigned long long nb, unsigned long long hi) {\n"
     << "extern __shared__ float2 tile[];\n"
     << "const unsigned tid = threadIdx.x;\n";
   o << "const unsigned ptl = " << thread_expr(pg.maps.front(), phys) << ";\n";

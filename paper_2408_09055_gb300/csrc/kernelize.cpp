@@ -87,8 +87,9 @@ struct Ctx {
 
   double kcost(const OpenK& k) const { return k.fusion ? cm.fusion(k.st) : cm.shm(k.st); }
   bool fits(const OpenK& k) const {
-    if (k.fusion) return std::popcount(k.q) <= kmax;
-    return std::popcount(k.ni | low) <= shm_max;
+    const uint64_t lim = cm.plan->exec_limit;
+    if (k.fusion) return std::popcount(k.q) <= kmax && !(k.q & ~lim);
+    return std::popcount(k.ni | low) <= shm_max && !((k.ni | low) & ~lim);
   }
   int32_t push(int kind, int32_t a, int32_t b, int32_t parent) {
     ev.push_back(Event{kind, a, b, parent});

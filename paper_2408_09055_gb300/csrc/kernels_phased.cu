@@ -21,6 +21,7 @@ namespace {
 struct V2Params {
   float2* psi;
   const uint32_t* prog;
+  uint64_t hi;  // known bits of qubits outside the addressed state (chunked execution)
   int n, nruns;
   uint8_t run_src[16], run_len[16], run_dst[16];
   uint32_t ld_er[kRegBits];
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(1 << (M - kRegBits), 1 << (kMaxShmActive - M))
     uint64_t base = 0;
     for (int r = 0; r < P.nruns; ++r)
       base |= ((bt >> P.run_src[r]) & ((1ull << P.run_len[r]) - 1ull)) << P.run_dst[r];
+    const uint64_t kbase = base | P.hi;  // for known-bit references only
     Amps a;
     {
       const float2* tp = P.psi + (base | ptl);
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(1 << (M - kRegBits), 1 << (kMaxShmActive - M))
             pm = B == 0 ? 0xAAAAAAAAu : B == 1 ? 0xCCCCCCCCu : B == 2 ? 0xF0F0F0F0u
                : B == 3 ? 0xFF00FF00u : 0xFFFF0000u;
           } else {
-            pm = known_bit(B, lt, base) ? 0xFFFFFFFFu : 0u;
+            pm = known_bit(B, lt, kbase) ? 0xFFFFFFFFu : 0u;
           }
           QS_SLOT(k_g1c, A, a, u00, u01, u10, u11, pm)
           pc += 9;
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(1 << (M - kRegBits), 1 << (kMaxShmActive - M))
           pc += 1;
           break;
         case PK_XGK:
-          if (known_bit(B, lt, base)) {
+          if (known_bit(B, lt, kbase)) {
             QS_SLOT(k_xg, A, a)
           }
           pc += 1;
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(1 << (M - kRegBits), 1 << (kMaxShmActive - M))
           break;
         }
         case PK_D1K: {
-          const uint32_t kb = known_bit(B, lt, base);
+          const uint32_t kb = known_bit(B, lt, kbase);
           const float2 e0 = ldc(pc + 1 + 4 * kb), e1 = ldc(pc + 3 + 4 * kb);
           const uint32_t u = (Cu >> (2 * kb)) & 3u;  // bit0: e0 is 1, bit1: e1 is 1
           if (u == 0) {
@@ -358,8 +360,8 @@ __global__ void __launch_bounds__(1 << (M - kRegBits), 1 << (kMaxShmActive - M))
           break;
         }
         case PK_D0: {
-          const uint32_t k0 = known_bit(A, lt, base);
-          const uint32_t k1 = (B == REF_NONE) ? 0u : known_bit(B, lt, base);
+          const uint32_t k0 = known_bit(A, lt, kbase);
+          const uint32_t k1 = (B == REF_NONE) ? 0u : known_bit(B, lt, kbase);
           const uint32_t idx = k0 | (k1 << 1);
           if (!((Cu >> idx) & 1u)) k_scale(a, ldc(pc + 1 + 2 * idx));
           pc += 9;
@@ -458,7 +460,7 @@ int launch_m(const V2Params& P, int n, cudaStream_t s) {
 
 }  // namespace
 
-int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, cudaStream_t s) {
+int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, uint64_t hi, cudaStream_t s) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -468,7 +470,8 @@ int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, cudaS
   const int bps = 1 << (kMaxShmActive - m);  // the kernels' launch bounds
   unsigned long long nb = 1ull << (n - m);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms * bps);
-  void* args[] = {&psi, &nb};
+  unsigned long long hiv = hi;
+  void* args[] = {&psi, &nb, &hiv};
   cudaError_t e = cudaLaunchKernel((const void*)k, dim3((unsigned)grid), dim3(threads), args, smem, s);
   if (e != cudaSuccess) {
     set_cuda_error("specialised shm kernel launch", e);
@@ -483,6 +486,7 @@ int launch_shm_v2(const ShmV2Launch& a, cudaStream_t s) {
   V2Params P;
   P.psi = a.psi;
   P.prog = a.prog;
+  P.hi = a.hi;
   P.n = a.n;
   P.nruns = pg.nruns;
   for (int r = 0; r < 16; ++r) {

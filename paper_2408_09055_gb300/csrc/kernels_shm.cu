@@ -20,6 +20,7 @@ constexpr int kThreads = 256;
 
 struct ShmParams {
   float2* psi;
+  uint64_t hi;  // known bits of qubits outside the addressed state
   const DevOp* ops;
   int nops;
   int n, m;
@@ -61,10 +62,11 @@ __global__ void __launch_bounds__(kThreads) shm_kernel_v1(ShmParams P) {
     for (int li = tid; li < L; li += kThreads)
       tile[li] = P.psi[base | tab[0][li & 31] | tab[1][(li >> 5) & 31] | tab[2][(li >> 10) & 31]];
     __syncthreads();
+    const uint64_t kbase = base | P.hi;  // for known-bit references only
     for (int o = 0; o < P.nops; ++o) {
       const DevOp& op = P.ops[o];
       const uint64_t cg = op.cglob;
-      if ((base & cg) != cg) continue;  // uniform over the block
+      if ((kbase & cg) != cg) continue;  // uniform over the block
       const uint8_t kind = op.kind;
       const uint32_t cl = op.cloc;
       if (kind == OP_DENSE1) {
@@ -104,8 +106,8 @@ __global__ void __launch_bounds__(kThreads) shm_kernel_v1(ShmParams P) {
         }
       } else {  // OP_DIAG
         const int t0 = op.t0, t1 = op.t1;
-        const int gb0 = op.g0 >= 0 ? (int)((base >> op.g0) & 1) : 0;
-        const int gb1 = op.g1 >= 0 ? (int)((base >> op.g1) & 1) : 0;
+        const int gb0 = op.g0 >= 0 ? (int)((kbase >> op.g0) & 1) : 0;
+        const int gb1 = op.g1 >= 0 ? (int)((kbase >> op.g1) & 1) : 0;
         float2 d[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) d[s] = make_float2(op.m[2 * s], op.m[2 * s + 1]);
@@ -132,6 +134,7 @@ int launch_shm(const ShmLaunch& a, cudaStream_t s) {
   if (a.m < 1 || a.m > kMaxShmActive || a.m > a.n) return QS_EINVAL;
   ShmParams P;
   P.psi = a.psi;
+  P.hi = a.hi;
   P.ops = a.ops;
   P.nops = a.nops;
   P.n = a.n;

@@ -33,6 +33,7 @@ double CostModel::fusion(const KStat& s) const {
   const auto& o = plan->opts;
   int k = popc(s.q);
   if (o.fuse_kmax <= 0 || k > o.fuse_kmax) return INF;
+  if (s.q & ~plan->exec_limit) return INF;
   if (learned) return learned_cost(learned, s, true);
   int ke = std::max(k, std::min(o.fuse_kmin, plan->n));  // widened to fuse_kmin
   return plan->cost.fuse_cost[ke];
@@ -41,7 +42,7 @@ double CostModel::fusion(const KStat& s) const {
 double CostModel::shm(const KStat& s) const {
   const auto& o = plan->opts;
   uint64_t a = s.ni | low_mask(o.forced_low, plan->n);
-  if (popc(a) > o.shm_max_active) return INF;
+  if (popc(a) > o.shm_max_active || (a & ~plan->exec_limit)) return INF;
   if (learned) return learned_cost(learned, s, false);
   return plan->cost.alpha + s.gcost;
 }
@@ -123,8 +124,9 @@ static int plan_ordered(PlanImpl* p) {
       KStat s;
       for (int64_t j = (int64_t)i; j >= 0; --j) {
         s.add(p->gates[j], 0.0);
-        const bool fok = p->opts.fuse_kmax > 0 && popc(s.q) <= p->opts.fuse_kmax;
-        const bool sok = popc(s.ni | low) <= p->opts.shm_max_active;
+        const bool fok = p->opts.fuse_kmax > 0 && popc(s.q) <= p->opts.fuse_kmax &&
+                         !(s.q & ~p->exec_limit);
+        const bool sok = popc(s.ni | low) <= p->opts.shm_max_active && !((s.ni | low) & ~p->exec_limit);
         if (!fok && !sok) break;
         if (fok) want.push_back({s, true});
         if (sok) want.push_back({s, false});

@@ -99,6 +99,9 @@ def _load():
         "qs_state_device_ptr": ([vp], vp),
         "qs_state_set_zero": ([vp, vp], ctypes.c_int),
         "qs_run_plan": ([vp, vp, vp], ctypes.c_int),
+        "qs_run_plan_host": ([vp, vp, vp, u64, vp], ctypes.c_int),
+        "qs_plan_stage": ([vp, i32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64), ip, ip],
+                          ctypes.c_int),
         "qs_timer_create": ([vp, u64, ctypes.POINTER(vp)], ctypes.c_int),
         "qs_run_plan_timed": ([vp, vp, vp, vp], ctypes.c_int),
         "qs_timer_read": ([vp, dp, u64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
@@ -231,6 +234,24 @@ class Plan:
     def validate(self, gates=None) -> int:
         g = self._gates if gates is None else _gates_array(gates)
         return _lib.qs_plan_validate(self.h, g.ctypes.data_as(ctypes.c_void_p), len(g))
+
+    def stage(self, i: int) -> dict:
+        """qs_plan_stage: local qubit mask, gate count and kernel range."""
+        mask, ng = ctypes.c_uint64(), ctypes.c_int64()
+        first, cnt = ctypes.c_int32(), ctypes.c_int32()
+        check(_lib.qs_plan_stage(self.h, int(i), ctypes.byref(mask), ctypes.byref(ng), ctypes.byref(first),
+                                 ctypes.byref(cnt)), "qs_plan_stage")
+        return {"local_mask": int(mask.value), "num_gates": int(ng.value),
+                "first_kernel": int(first.value), "num_kernels": int(cnt.value)}
+
+    def stages(self) -> list[dict]:
+        return [self.stage(i) for i in range(self.stats().num_stages)]
+
+    def run_host(self, host_ptr: int, device_buffer: int = 0, buffer_bytes: int = 0, stream=None):
+        """qs_run_plan_host: applies the plan to a page-locked host state
+        (2^n complex64) chunk by chunk; asynchronous on `stream`."""
+        check(_lib.qs_run_plan_host(self.h, ctypes.c_void_p(host_ptr), ctypes.c_void_p(device_buffer or None),
+                                    int(buffer_bytes), _stream_ptr(stream)), "qs_run_plan_host")
 
 
 class Timer:
