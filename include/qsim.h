@@ -229,6 +229,23 @@ int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream);
 int qs_run_plan_host(const qs_plan* plan, float* host_state, void* device_buffer,
                      uint64_t buffer_bytes, void* stream);
 
+/* Timeline of one qs_run_plan_host call, from CUDA events on the internal
+ * streams.  A timer holds events for every (stage, chunk) record of its
+ * plan (stages x 2^(n-L) records, at most 65536, else QS_EINVAL).
+ * qs_run_plan_host_timed runs like qs_run_plan_host and records, per
+ * record: copy-in start, copy-in end (= kernels start), kernels end
+ * (= copy-out start), copy-out end.  qs_host_timer_read synchronises and
+ * writes those 4 times per record, in ms since the call started on
+ * `stream`, into ms[0 .. 4*nrec) (stage-major, then chunk), and nrec.  The
+ * events add a little work on the streams; timings of the untimed call are
+ * those of the whole call (events around it on `stream`).                  */
+typedef struct qs_host_timer qs_host_timer;
+int qs_host_timer_create(const qs_plan* plan, qs_host_timer** out);
+int qs_run_plan_host_timed(const qs_plan* plan, float* host_state, void* device_buffer,
+                           uint64_t buffer_bytes, qs_host_timer* timer, void* stream);
+int qs_host_timer_read(qs_host_timer* timer, double* ms, uint64_t cap, uint64_t* nrec);
+void qs_host_timer_free(qs_host_timer* timer);
+
 /* Per-kernel timing with CUDA events on the launching stream (used by the
  * benchmark for the roofline of each kernel type).  A timer holds
  * (num_kernels + 1) * max_runs events; qs_run_plan_timed records one event

@@ -647,8 +647,79 @@ static int run_plan_impl(const qs_plan* plan, qs_state* st, void* stream, qs_tim
 
 // ---- host-resident state: Alg. 1's Execute with the shards in host memory ----
 
+struct qs_host_timer {
+  const qs_plan* plan = nullptr;
+  uint64_t nrec = 0;                // stages x chunks
+  std::vector<cudaEvent_t> ev;      // 1 + 4 per record
+  bool recorded = false;
+};
+
+static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* device_buffer,
+                              uint64_t buffer_bytes, void* stream, qs_host_timer* tm);
+
 int qs_run_plan_host(const qs_plan* plan, float* host_state, void* device_buffer,
                      uint64_t buffer_bytes, void* stream) {
+  return run_plan_host_impl(plan, host_state, device_buffer, buffer_bytes, stream, nullptr);
+}
+
+static uint64_t host_records(const qs_plan* plan) {
+  const uint64_t stages = plan->stages.empty() ? 1 : plan->stages.size();
+  const int L = plan->stages.empty() ? plan->impl.n : plan->impl.opts.local_qubits;
+  return stages << (plan->impl.n - L);
+}
+
+int qs_host_timer_create(const qs_plan* plan, qs_host_timer** out) {
+  if (!plan || !out) return QS_EINVAL;
+  *out = nullptr;
+  const uint64_t nrec = host_records(plan);
+  if (nrec > kMaxHostTimerRecords) return QS_EINVAL;
+  qs_host_timer* t = new (std::nothrow) qs_host_timer();
+  if (!t) return QS_ENOMEM;
+  t->plan = plan;
+  t->nrec = nrec;
+  t->ev.assign(1 + 4 * nrec, nullptr);
+  for (auto& e : t->ev) {
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) {
+      qs_host_timer_free(t);
+      return cuda_status(r);
+    }
+  }
+  *out = t;
+  return QS_OK;
+}
+
+void qs_host_timer_free(qs_host_timer* t) {
+  if (!t) return;
+  for (auto e : t->ev)
+    if (e) cudaEventDestroy(e);
+  delete t;
+}
+
+int qs_run_plan_host_timed(const qs_plan* plan, float* host_state, void* device_buffer,
+                           uint64_t buffer_bytes, qs_host_timer* t, void* stream) {
+  if (!t || t->plan != plan) return QS_EINVAL;
+  return run_plan_host_impl(plan, host_state, device_buffer, buffer_bytes, stream, t);
+}
+
+int qs_host_timer_read(qs_host_timer* t, double* ms, uint64_t cap, uint64_t* nrec) {
+  if (!t || !nrec) return QS_EINVAL;
+  if (!t->recorded) return QS_EINVAL;
+  if (!ms || cap < 4 * t->nrec) return QS_EINVAL;
+  cudaError_t e = cudaEventSynchronize(t->ev[0]);
+  for (uint64_t i = 0; i < 4 * t->nrec && e == cudaSuccess; ++i) {
+    float v = 0;
+    e = cudaEventSynchronize(t->ev[1 + i]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t->ev[0], t->ev[1 + i]);
+    ms[i] = v;
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  *nrec = t->nrec;
+  return QS_OK;
+}
+
+static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* device_buffer,
+                              uint64_t buffer_bytes, void* stream, qs_host_timer* tm) {
   if (!plan || !host_state) return QS_EINVAL;
   if (reinterpret_cast<uintptr_t>(host_state) & 15) return QS_EINVAL;
   const PlanImpl& P = plan->impl;
@@ -695,6 +766,10 @@ int qs_run_plan_host(const qs_plan* plan, float* host_state, void* device_buffer
     fail(cudaStreamCreateWithFlags(&ss[b], cudaStreamNonBlocking));
   for (int b = 0; b <= nbuf && rc == QS_OK; ++b)
     fail(cudaEventCreateWithFlags(&evs[b], cudaEventDisableTiming));
+  if (tm) {
+    tm->recorded = false;
+    if (rc == QS_OK) fail(cudaEventRecord(tm->ev[0], user));
+  }
   // the internal streams start after the caller's stream
   if (rc == QS_OK && !fail(cudaEventRecord(evs[nbuf], user)))
     for (int b = 0; b < nbuf && rc == QS_OK; ++b) fail(cudaStreamWaitEvent(ss[b], evs[nbuf], 0));
@@ -709,32 +784,58 @@ int qs_run_plan_host(const qs_plan* plan, float* host_state, void* device_buffer
   }
   float2* hs = reinterpret_cast<float2*>(host_state);
   const uint64_t nch = 1ull << nchunks_log;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int max_pitch = 0;
+  cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxPitch, dev);
   for (size_t si = 0; si < plans.size() && rc == QS_OK; ++si) {
     const Stage* st = staged ? &plan->stages[si] : nullptr;
+    // A chunk is 2^(L - run_log) host runs of 2^run_log amplitudes; the
+    // local qubits above run_log, ascending, index the runs.  The lowest
+    // `g` of them are consecutive qubits, so those runs are evenly spaced in
+    // host memory (pitch 2^q0 amplitudes) and move with one 2D copy.
     const int run_log = staged ? st->run_log : n;
     const uint64_t run_amps = 1ull << run_log;
-    const uint64_t nruns = 1ull << (L - run_log);
-    // host index of the chunk's regional bits / of run r's local high bits
+    int g = 0;
+    if (staged)
+      while (run_log + g + 1 < L && st->order[run_log + g + 1] == st->order[run_log] + g + 1) ++g;
+    if (staged && run_log < L) ++g;  // the group holds order[run_log .. run_log + g - 1]
+    const uint64_t hpitch = staged && run_log < L ? (sizeof(float2) << st->order[run_log]) : 0;
+    if (hpitch == 0 || hpitch > (uint64_t)max_pitch) g = 0;
+    const uint64_t rows = 1ull << g;
+    const uint64_t nouter = 1ull << (L - run_log - g);
     auto deposit = [&](uint64_t v, int from, int count) {
       uint64_t x = 0;
       for (int t = 0; t < count; ++t)
         if ((v >> t) & 1) x |= 1ull << st->order[from + t];
       return x;
     };
+    auto copy = [&](float2* d, uint64_t hbase, cudaStream_t s, bool in) {
+      for (uint64_t r = 0; r < nouter && rc == QS_OK; ++r) {
+        const uint64_t h = hbase | (staged ? deposit(r << g, run_log, L - run_log) : 0);
+        float2* dp = d + ((r << g) << run_log);
+        const size_t w = run_amps * sizeof(float2);
+        if (rows == 1)
+          fail(in ? cudaMemcpyAsync(dp, hs + h, w, cudaMemcpyHostToDevice, s)
+                  : cudaMemcpyAsync(hs + h, dp, w, cudaMemcpyDeviceToHost, s));
+        else
+          fail(in ? cudaMemcpy2DAsync(dp, w, hs + h, hpitch, w, rows, cudaMemcpyHostToDevice, s)
+                  : cudaMemcpy2DAsync(hs + h, hpitch, dp, w, w, rows, cudaMemcpyDeviceToHost, s));
+      }
+    };
     for (uint64_t c = 0; c < nch && rc == QS_OK; ++c) {
       const int b = (int)(c % (uint64_t)nbuf);
       const cudaStream_t s = ss[b];
       float2* d = dbuf + (uint64_t(b) << L);
       const uint64_t hbase = staged ? deposit(c, L, n - L) : 0;
-      for (uint64_t r = 0; r < nruns && rc == QS_OK; ++r) {
-        const uint64_t h = hbase | (staged ? deposit(r, run_log, L - run_log) : 0);
-        fail(cudaMemcpyAsync(d + (r << run_log), hs + h, run_amps * sizeof(float2), cudaMemcpyHostToDevice, s));
-      }
+      cudaEvent_t* te = tm ? &tm->ev[1 + 4 * (si * nch + c)] : nullptr;
+      if (te && rc == QS_OK) fail(cudaEventRecord(te[0], s));
+      copy(d, hbase, s, true);
+      if (te && rc == QS_OK) fail(cudaEventRecord(te[1], s));
       if (rc == QS_OK) rc = run_kernels(plans[si], dcs[si], d, L, c << L, s, nullptr);
-      for (uint64_t r = 0; r < nruns && rc == QS_OK; ++r) {
-        const uint64_t h = hbase | (staged ? deposit(r, run_log, L - run_log) : 0);
-        fail(cudaMemcpyAsync(hs + h, d + (r << run_log), run_amps * sizeof(float2), cudaMemcpyDeviceToHost, s));
-      }
+      if (te && rc == QS_OK) fail(cudaEventRecord(te[2], s));
+      copy(d, hbase, s, false);
+      if (te && rc == QS_OK) fail(cudaEventRecord(te[3], s));
     }
     // a stage reads what every chunk of the previous stage wrote back
     if (si + 1 < plans.size() && nbuf > 1) {
@@ -753,6 +854,7 @@ int qs_run_plan_host(const qs_plan* plan, float* host_state, void* device_buffer
     if (ss[b]) cudaStreamDestroy(ss[b]);
   for (int b = 0; b <= nbuf; ++b)
     if (evs[b]) cudaEventDestroy(evs[b]);
+  if (tm && rc == QS_OK) tm->recorded = true;
   return rc;
 }
 

@@ -100,6 +100,10 @@ def _load():
         "qs_state_set_zero": ([vp, vp], ctypes.c_int),
         "qs_run_plan": ([vp, vp, vp], ctypes.c_int),
         "qs_run_plan_host": ([vp, vp, vp, u64, vp], ctypes.c_int),
+        "qs_host_timer_create": ([vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "qs_run_plan_host_timed": ([vp, vp, vp, u64, vp, vp], ctypes.c_int),
+        "qs_host_timer_read": ([vp, dp, u64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "qs_host_timer_free": ([vp], None),
         "qs_plan_stage": ([vp, i32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64), ip, ip],
                           ctypes.c_int),
         "qs_timer_create": ([vp, u64, ctypes.POINTER(vp)], ctypes.c_int),
@@ -275,6 +279,38 @@ class Timer:
         check(_lib.qs_timer_read(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size,
                                  ctypes.byref(runs)), "qs_timer_read")
         return out[:nk], int(runs.value)
+
+
+class HostTimer:
+    """Per-chunk timeline of a staged host run (qs_host_timer_*)."""
+
+    def __init__(self, plan: Plan):
+        h = ctypes.c_void_p()
+        check(_lib.qs_host_timer_create(plan.h, ctypes.byref(h)), "qs_host_timer_create")
+        self.h = h
+        self.plan = plan
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.qs_host_timer_free(self.h)
+            self.h = None
+
+    def run(self, host_ptr: int, device_buffer: int = 0, buffer_bytes: int = 0, stream=None):
+        check(_lib.qs_run_plan_host_timed(self.plan.h, ctypes.c_void_p(host_ptr),
+                                          ctypes.c_void_p(device_buffer or None), int(buffer_bytes), self.h,
+                                          _stream_ptr(stream)), "qs_run_plan_host_timed")
+
+    def read(self) -> np.ndarray:
+        """Array [stages, chunks, 4] of ms since the call began: copy-in
+        start, kernels start, copy-out start, copy-out end."""
+        st = self.plan.stats()
+        nrec = ctypes.c_uint64()
+        L = self.plan.opts.local_qubits if 0 < self.plan.opts.local_qubits < self.plan.n else self.plan.n
+        cap = st.num_stages << (self.plan.n - L)
+        out = np.zeros(4 * cap, dtype=np.float64)
+        check(_lib.qs_host_timer_read(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size,
+                                      ctypes.byref(nrec)), "qs_host_timer_read")
+        return out.reshape(st.num_stages, -1, 4)
 
 
 class State:
