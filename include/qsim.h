@@ -210,14 +210,15 @@ int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream);
  * chunk of 2^L amplitudes that share one value of the stage's regional
  * qubits, copy the chunk to the GPU, run the stage's kernels on it (the
  * regional values are known bits of insular gates, Definition 2) and copy
- * it back.  Chunks are double or triple buffered over internal streams, so
- * copies in both directions overlap the kernels of the neighbouring chunks;
- * a stage starts after every chunk of the previous one is back.
+ * it back.  Chunks rotate over up to 4 buffers on internal streams, so
+ * copies in both directions overlap the kernels of the neighbouring chunks.
+ * A chunk's copy-in waits only for the chunks of the previous stage its
+ * amplitudes come from, so consecutive stages overlap at their boundary.
  *   host_state   2^n complex64 amplitudes (interleaved float pairs), updated
  *                in place; page-locked (cudaMallocHost / cudaHostRegister),
  *                16-byte aligned, else QS_EINVAL.  Caller-owned.
  *   device_buffer, buffer_bytes
- *                device scratch for min(3, buffer_bytes / (8 * 2^L)) chunk
+ *                device scratch for min(4, buffer_bytes / (8 * 2^L)) chunk
  *                buffers (>= 1, 256-byte aligned), caller-owned; NULL: the
  *                library allocates two (one when L = n) stream-ordered for
  *                the call.

@@ -788,8 +788,21 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
   cudaGetDevice(&dev);
   int max_pitch = 0;
   cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxPitch, dev);
+  // done[parity][c]: chunk c of the last stage of that parity is back in
+  // host memory.  A chunk of the next stage waits only for the chunks its
+  // amplitudes come from, so stages overlap at their boundary.
+  const bool multi = plans.size() > 1;
+  std::vector<cudaEvent_t> done[2];
+  if (multi)
+    for (auto& v : done) {
+      v.assign(nch, nullptr);
+      for (auto& e : v)
+        if (rc == QS_OK) fail(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+  uint64_t gchunk = 0;  // chunks take the buffers round-robin across stages
   for (size_t si = 0; si < plans.size() && rc == QS_OK; ++si) {
     const Stage* st = staged ? &plan->stages[si] : nullptr;
+    const Stage* prev = staged && si > 0 ? &plan->stages[si - 1] : nullptr;
     // A chunk is 2^(L - run_log) host runs of 2^run_log amplitudes; the
     // local qubits above run_log, ascending, index the runs.  The lowest
     // `g` of them are consecutive qubits, so those runs are evenly spaced in
@@ -823,28 +836,58 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
                   : cudaMemcpy2DAsync(hs + h, hpitch, dp, w, w, rows, cudaMemcpyDeviceToHost, s));
       }
     };
-    for (uint64_t c = 0; c < nch && rc == QS_OK; ++c) {
-      const int b = (int)(c % (uint64_t)nbuf);
+    // copy-in after a stage boundary: units of 2^jin amplitudes, each inside
+    // one chunk of the previous stage (a previous regional qubit below
+    // run_log splits the runs), issued source chunk by source chunk
+    int jin = run_log;
+    if (prev)
+      for (int k = L; k < n; ++k)
+        if (prev->order[k] < jin && ((st->local >> prev->order[k]) & 1)) jin = prev->order[k];
+    const uint64_t nunits = prev ? 1ull << (L - jin) : 0;
+    auto source_of = [&](uint64_t h) {
+      uint64_t c = 0;
+      for (int k = L; k < n; ++k) c |= ((h >> prev->order[k]) & 1ull) << (k - L);
+      return c;
+    };
+    std::vector<std::pair<uint64_t, uint64_t>> units;  // (source chunk, unit index)
+    for (uint64_t c = 0; c < nch && rc == QS_OK; ++c, ++gchunk) {
+      const int b = (int)(gchunk % (uint64_t)nbuf);
       const cudaStream_t s = ss[b];
       float2* d = dbuf + (uint64_t(b) << L);
       const uint64_t hbase = staged ? deposit(c, L, n - L) : 0;
       cudaEvent_t* te = tm ? &tm->ev[1 + 4 * (si * nch + c)] : nullptr;
       if (te && rc == QS_OK) fail(cudaEventRecord(te[0], s));
-      copy(d, hbase, s, true);
+      if (!prev) {
+        copy(d, hbase, s, true);
+      } else {
+        units.clear();
+        for (uint64_t u = 0; u < nunits; ++u) {
+          const uint64_t h = hbase | deposit(u, jin, L - jin);
+          units.push_back({source_of(h), u});
+        }
+        std::sort(units.begin(), units.end());
+        uint64_t waited = ~0ull;
+        for (const auto& [src, u] : units) {
+          if (rc != QS_OK) break;
+          if (src != waited) {
+            fail(cudaStreamWaitEvent(s, done[(si - 1) & 1][src], 0));
+            waited = src;
+          }
+          const uint64_t h = hbase | deposit(u, jin, L - jin);
+          fail(cudaMemcpyAsync(d + (u << jin), hs + h, sizeof(float2) << jin, cudaMemcpyHostToDevice, s));
+        }
+      }
       if (te && rc == QS_OK) fail(cudaEventRecord(te[1], s));
       if (rc == QS_OK) rc = run_kernels(plans[si], dcs[si], d, L, c << L, s, nullptr);
       if (te && rc == QS_OK) fail(cudaEventRecord(te[2], s));
       copy(d, hbase, s, false);
       if (te && rc == QS_OK) fail(cudaEventRecord(te[3], s));
-    }
-    // a stage reads what every chunk of the previous stage wrote back
-    if (si + 1 < plans.size() && nbuf > 1) {
-      for (int b = 0; b < nbuf && rc == QS_OK; ++b) fail(cudaEventRecord(evs[b], ss[b]));
-      for (int b = 0; b < nbuf && rc == QS_OK; ++b)
-        for (int o = 0; o < nbuf && rc == QS_OK; ++o)
-          if (o != b) fail(cudaStreamWaitEvent(ss[b], evs[o], 0));
+      if (multi && rc == QS_OK) fail(cudaEventRecord(done[si & 1][c], s));
     }
   }
+  for (auto& v : done)
+    for (auto e : v)
+      if (e) cudaEventDestroy(e);
   // join: the caller's stream continues after every chunk is back in host memory
   for (int b = 1; b < nbuf; ++b)
     if (ss[b] && evs[b] && cudaEventRecord(evs[b], ss[b]) == cudaSuccess) cudaStreamWaitEvent(ss[0], evs[b], 0);

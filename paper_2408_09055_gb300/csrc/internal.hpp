@@ -174,7 +174,7 @@ struct Stage {
 // lowest qubits, stay local in every stage so host runs are 2^(L-8) long
 constexpr int kStageSlots = 8;
 constexpr int kMinLocalQubits = 12;
-constexpr int kMaxChunkBuffers = 3;  // copy-in / compute / copy-out in flight
+constexpr int kMaxChunkBuffers = 4;  // chunks in flight: copy-in, kernels, copy-out, slack
 constexpr uint64_t kMaxHostTimerRecords = 1ull << 16;  // stages x chunks of a timed host run  // a chunk holds a 2^12 tile and a tensor-core kernel
 int stage_circuit(const std::vector<Gate>& gates, int n, int L, std::vector<Stage>* out);
 

@@ -50,7 +50,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("nbuf", [None, 1, 2, 3])
+@pytest.mark.parametrize("nbuf", [None, 1, 2, 3, 4])
 @pytest.mark.parametrize("case", list(CASES))
 def test_staged_plans_match_oracle(case, nbuf):
     need_gpu()
@@ -63,8 +63,8 @@ def test_staged_plans_match_oracle(case, nbuf):
     assert_close_state(got, sim.apply(n, g))
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
-def test_staged_random_initial_state(variant):
+@pytest.mark.parametrize("variant,nbuf", [(1, 2), (2, 3), (3, 4), (3, 1)])
+def test_staged_random_initial_state(variant, nbuf):
     # every amplitude nonzero: a chunk gathered or scattered to the wrong
     # host run shows up element by element
     need_gpu()
@@ -73,7 +73,8 @@ def test_staged_random_initial_state(variant):
     g = C.mixed_circuit(n, 500, 8)
     psi0 = random_state(n, 9)
     plan = Q.Plan(n, g, local_qubits=L, shm_max_active=12, shm_variant=variant)
-    got = run_host(plan, n, psi0, nbuf=2)
+    assert plan.stats().num_stages > 3
+    got = run_host(plan, n, psi0, nbuf=nbuf)
     assert_close_state(got, sim.apply(n, g, psi0.copy()))
 
 
@@ -134,3 +135,35 @@ def test_staged_30_qubits_circuit_then_adjoint_returns_to_zero():
     f = fidelity(ref, got)
     assert f >= 1 - 1e-6, f
     assert float(np.max(np.abs(got[1:]))) <= 1e-5
+
+
+def test_many_small_chunks_and_stages():
+    # 2^8 chunks per stage: the chunk-level waits between stages, the buffer
+    # rotation across stages and the unit split of copy-ins at every boundary
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n, L = 20, 12
+    g = C.mixed_circuit(n, 300, 31)
+    psi0 = random_state(n, 32)
+    plan = Q.Plan(n, g, local_qubits=L, shm_max_active=12)
+    assert plan.stats().num_stages > 5
+    got = run_host(plan, n, psi0, nbuf=3)
+    assert_close_state(got, sim.apply(n, g, psi0.copy()))
+
+
+def test_host_timer_timeline_is_ordered():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n, L = 18, 14
+    g = C.mixed_circuit(n, 300, 41)
+    plan = Q.Plan(n, g, local_qubits=L)
+    h, v = pinned_state(n)
+    dev = torch.empty(3 << (L + 1), dtype=torch.float32, device="cuda")
+    tm = Q.HostTimer(plan)
+    s = torch.cuda.current_stream()
+    tm.run(h.data_ptr(), dev.data_ptr(), dev.numel() * 4, stream=s.cuda_stream)
+    s.synchronize()
+    T = tm.read()
+    assert T.shape == (plan.stats().num_stages, 1 << (n - L), 4)
+    assert np.all(T >= 0) and np.all(np.diff(T, axis=2) >= 0)
+    assert_close_state(v.copy(), sim.apply(n, g))
