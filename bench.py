@@ -311,8 +311,8 @@ def staged_measure(args):
     plan_s = time.perf_counter() - t0
     ps = plan.stats()
     host = torch.empty(2 << n, dtype=torch.float32, pin_memory=True)
-    nbuf = 3
-    dev = torch.empty(nbuf << (L + 1), dtype=torch.float32, device="cuda")
+    nbuf = args.chunk_buffers
+    dev = torch.empty(max(nbuf, 2) << (L + 1), dtype=torch.float32, device="cuda")
     chunk = 8 << L
     peaks_c = _copy_peaks(torch, host, dev, min(chunk, 4 << 30))  # before the state is set
     host.zero_()
@@ -320,7 +320,7 @@ def staged_measure(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     for _ in range(args.warmup):
-        plan.run_host(host.data_ptr(), dev.data_ptr(), dev.numel() * 4, stream=sp)
+        plan.run_host(host.data_ptr(), dev.data_ptr(), nbuf * (8 << L), stream=sp)
     torch.cuda.synchronize()
     clocks = ClockSampler(_env_int("LOCAL_RANK", 0))
     clocks.start()
@@ -328,11 +328,20 @@ def staged_measure(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.run_host(host.data_ptr(), dev.data_ptr(), dev.numel() * 4, stream=sp)
+        plan.run_host(host.data_ptr(), dev.data_ptr(), nbuf * (8 << L), stream=sp)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    # one more run with the per-chunk timeline: where the time goes
+    tm = Q.HostTimer(plan)
+    tm.run(host.data_ptr(), dev.data_ptr(), nbuf * (8 << L), stream=sp)
+    torch.cuda.synchronize()
+    T = tm.read()
+    breakdown = {"timeline_ms": float(T[:, :, 3].max()),
+                 "copy_in_ms": float((T[:, :, 1] - T[:, :, 0]).sum()),
+                 "kernels_ms": float((T[:, :, 2] - T[:, :, 1]).sum()),
+                 "copy_out_ms": float((T[:, :, 3] - T[:, :, 2]).sum())}
     v = host.numpy().view(np.complex64)
     norm = 0.0
     for a in range(0, v.size, 1 << 26):
@@ -354,6 +363,7 @@ def staged_measure(args):
                      "frac": achieved / peaks_c["both"], "traffic": moved,
                      "peak_source": "measured here: concurrent H2D + D2H copies of one chunk"},
         "copy_peaks_gbs": peaks_c,
+        "breakdown": breakdown,
         "gpu_launches": int(ps.num_kernels) * (1 << (n - L)) * args.steps,
         "clocks": clk, "norm2_after": norm,
         "e2e": {"value": ms, "unit": "ms/circuit", "h2d_bytes_per_step": int(ps.num_stages * (8 << n)),
@@ -383,6 +393,7 @@ def main():
                     help="measure staged execution instead: an N-qubit state in page-locked host "
                          "memory, run chunk by chunk with --local-qubits L")
     ap.add_argument("--local-qubits", type=int, default=0)
+    ap.add_argument("--chunk-buffers", type=int, default=4, choices=[1, 2, 3, 4])
     args = ap.parse_args()
     if args.staged:
         return staged_measure(args)
