@@ -31,7 +31,6 @@ namespace {
 constexpr int kTcK = 6;                // target qubits handled by the kernel
 constexpr int kTcDim = 1 << kTcK;      // 64 complex rows
 constexpr int kTcKR = 2 * kTcDim;      // 128: the real block's M = K
-constexpr int kTcThreads = 256;
 constexpr uint32_t kCoreStride = (kTcKR / 4) * 128;  // bytes between 8-row groups
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on an mbarrier wait
 
@@ -41,6 +40,7 @@ struct TcParams {
   float2* psi;
   const float* w;  // W (hi, then lo for 3xTF32) in the core layout
   int n;
+  int contig;      // the column qubits are 0..CB-1: output rows are contiguous
   uint64_t fixed;  // target and column qubits
   int8_t targets[kTcK];
   int8_t cols[8];
@@ -90,22 +90,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Waits for the mbarrier phase `parity`; false if the bound expired.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  const unsigned long long t0 = global_ns();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
-  }
-}
-
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -128,51 +112,95 @@ __host__ __device__ constexpr uint32_t core_off(uint32_t m, uint32_t kk) {
   return (m >> 3) * kCoreStride + (kk >> 2) * 128u + (m & 7u) * 16u + (kk & 3u) * 4u;
 }
 
-template <int CB, bool X3>
-__global__ void __launch_bounds__(kTcThreads, X3 ? 1 : 2) fused_tc_kernel(const __grid_constant__ TcParams P) {
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (*abort_flag || global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// Persistent, warp-specialised kernel.  Rows and columns of the real block
+// operands are ordered (re, im)-interleaved: K index 2j + r multiplies the
+// real (r = 0) or imaginary (r = 1) part of input row j, and M index 2j' + r'
+// produces the real or imaginary part of output row j'.  So a float2
+// amplitude is one 8-byte operand store, and output lanes 2j', 2j'+1 of a
+// warp hold one complex row.
+//   warps 0..7   producers: gather a tile (the next one's loads in flight),
+//                round to TF32 (hi, and lo for 3xTF32) into a ring of ST
+//                shared-memory stages;
+//   warps 8..11  drain: TMEM accumulator -> registers -> global (one warp
+//                per TMEM lane quadrant);
+//   warp 12      one thread issues the MMAs into two TMEM accumulators.
+constexpr int kProdWarps = 8;
+constexpr int kDrainWarps = 4;
+constexpr int kTcThreads2 = 32 * (kProdWarps + kDrainWarps + 1);
+
+template <int CB, bool X3, int ST>
+__global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_constant__ TcParams P) {
   constexpr int N = 1 << CB;
+  constexpr int NOP = X3 ? 2 : 1;
   constexpr uint32_t A_FLOATS = kTcKR * kTcKR;
   constexpr uint32_t B_FLOATS = N * kTcKR;
-  constexpr int DP = N + 1;  // padded pitch of the output staging tile
+  constexpr int TASKS = (N / 8) * (kTcDim / 4);  // warp accesses per tile: 8 columns x 4 rows
+  constexpr int EPT = TASKS / kProdWarps;        // per producer thread
   extern __shared__ __align__(1024) float smem[];
-  float* Ah = smem;
-  float* Al = smem + A_FLOATS;  // used with X3
-  float* Bh = smem + (X3 ? 2 : 1) * A_FLOATS;
-  float* Bl = Bh + B_FLOATS;    // used with X3
-  float* Dsm = Bh;              // output staging reuses the B region
-  __shared__ __align__(8) uint64_t mbar;
+  float* Aop = smem;
+  float* Bop = smem + NOP * A_FLOATS;  // stage s: hi at s*NOP*B_FLOATS, lo after it
+  __shared__ __align__(8) uint64_t bar_full[ST], bar_empty[ST], bar_accf[2], bar_acce[2], bar_fin;
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_all;
+  __shared__ volatile int abort_all;
   __shared__ unsigned long long rowoff[kTcDim];
   __shared__ unsigned long long coloff[N];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   {  // unitary (host-arranged in the core layout) into shared memory
     const float4* src = reinterpret_cast<const float4*>(P.w);
-    float4* dst = reinterpret_cast<float4*>(Ah);
-    for (uint32_t i = tid; i < (X3 ? 2 : 1) * A_FLOATS / 4; i += kTcThreads) dst[i] = src[i];
+    float4* dst = reinterpret_cast<float4*>(Aop);
+    for (uint32_t i = tid; i < NOP * A_FLOATS / 4; i += kTcThreads2) dst[i] = src[i];
   }
-  for (int r = tid; r < kTcDim; r += kTcThreads) {
+  for (int r = tid; r < kTcDim; r += kTcThreads2) {
     unsigned long long o = 0;
     for (int j = 0; j < kTcK; ++j)
       if ((r >> j) & 1) o |= 1ull << P.targets[j];
     rowoff[r] = o;
   }
-  for (int c = tid; c < N; c += kTcThreads) {
+  for (int c = tid; c < N; c += kTcThreads2) {
     unsigned long long o = 0;
     for (int j = 0; j < CB; ++j)
       if ((c >> j) & 1) o |= 1ull << P.cols[j];
     coloff[c] = o;
   }
-  const uint32_t mb = smem_u32(&mbar);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    for (int s = 0; s < ST; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[s])),
+                   "r"(32 * kProdWarps) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[s])) : "memory");
+    }
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_accf[a])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_acce[a])),
+                   "r"(32 * kDrainWarps) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_fin)) : "memory");
     abort_all = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base)),
-                 "r"((uint32_t)N)
+                 "r"((uint32_t)(2 * N))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -180,10 +208,7 @@ __global__ void __launch_bounds__(kTcThreads, X3 ? 1 : 2) fused_tc_kernel(const 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  uint32_t parity = 0;
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
-  constexpr int E = kTcDim * N / kTcThreads;  // tile elements per thread
-  const int lane = tid & 31;
   auto tile_base = [&](uint64_t bt) {
     uint64_t base = 0, x = bt;
     for (int q = 0; q < P.n && x; ++q)
@@ -193,138 +218,174 @@ __global__ void __launch_bounds__(kTcThreads, X3 ? 1 : 2) fused_tc_kernel(const 
       }
     return base;
   };
-  // element i of this thread: column c, row j (8 consecutive columns x 4 rows
-  // per warp access: 64-byte global runs, conflict-free operand stores)
-  auto elem = [&](int i, int& c, int& j) {
-    const int wq = (tid >> 5) + (kTcThreads / 32) * i;
-    c = (lane & 7) + 8 * (wq % (N / 8));
-    j = (lane >> 3) + 4 * (wq / (N / 8));
+  auto fail = [&]() {
+    abort_all = 1;
+    atomicExch(&g_tc_error, 1);
   };
-  float2 v[E];
-  auto load_tile = [&](uint64_t base) {
+
+  if (warp < kProdWarps) {
+    // ---- producers ----
+    float2 cur[EPT], nxt[EPT];
+    auto load = [&](uint64_t bt, float2 (&v)[EPT]) {
+      const uint64_t base = tile_base(bt);
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      int c, j;
-      elem(i, c, j);
-      v[i] = P.psi[base | rowoff[j] | coloff[c]];
-    }
-  };
-  // registers -> B operand (real block rows: Re 0..63, Im 64..127), then MMAs
-  auto stage_and_issue = [&]() {
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-      int c, j;
-      elem(i, c, j);
-      const uint32_t ore = core_off(c, j) >> 2, oim = core_off(c, j + kTcDim) >> 2;
-      const float hr = tf32_rna(v[i].x), hi = tf32_rna(v[i].y);
-      Bh[ore] = hr;
-      Bh[oim] = hi;
-      if (X3) {
-        Bl[ore] = v[i].x - hr;
-        Bl[oim] = v[i].y - hi;
+      for (int e = 0; e < EPT; ++e) {
+        const int task = warp + kProdWarps * e;
+        const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
+        v[e] = P.psi[base | rowoff[j] | coloff[c]];
       }
+    };
+    uint32_t it = 0;
+    uint64_t bt = blockIdx.x;
+    if (bt < nb) load(bt, cur);
+    for (; bt < nb; bt += gridDim.x, ++it) {
+      const uint64_t bn = bt + gridDim.x;
+      if (bn < nb) load(bn, nxt);
+      const uint32_t s = it % ST, ph = (it / ST) & 1u;
+      const bool ok = mbar_wait_or_abort(smem_u32(&bar_empty[s]), ph ^ 1u, &abort_all);
+      if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together
+        fail();
+        break;
+      }
+      float* bh = Bop + s * NOP * B_FLOATS;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int task = warp + kProdWarps * e;
+        const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
+        const uint32_t o = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
+        const float hr = tf32_rna(cur[e].x), hi = tf32_rna(cur[e].y);
+        *reinterpret_cast<float2*>(bh + o) = make_float2(hr, hi);
+        if (X3) *reinterpret_cast<float2*>(bh + B_FLOATS + o) = make_float2(cur[e].x - hr, cur[e].y - hi);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_full[s]));
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) cur[e] = nxt[e];
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else if (warp < kProdWarps + kDrainWarps) {
+    // ---- drain ----
+    const int q = warp & 3;  // TMEM lane quadrant of this warp
+    const int jrow = 16 * q + (lane >> 1);
+    const bool odd = lane & 1;
+    uint32_t it = 0;
+    for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x, ++it) {
+      const uint32_t a = it & 1u, pa = (it >> 1) & 1u;
+      const bool ok = mbar_wait_or_abort(smem_u32(&bar_accf[a]), pa, &abort_all);
+      if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together
+        fail();
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      constexpr uint32_t ID = idesc_tf32<N>();
-      const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), bh = smem_u32(Bh), bl = smem_u32(Bl);
-#pragma unroll 1
-      for (int s = 0; s < kTcKR / 8; ++s) {  // K = 8 per instruction: two core matrices
-        const uint32_t ks = (uint32_t)s * 256u;
-        mma_tf32(tmem, smem_desc(ah + ks), smem_desc(bh + ks), ID, s > 0);
-        if (X3) {
-          mma_tf32(tmem, smem_desc(ah + ks), smem_desc(bl + ks), ID, 1);
-          mma_tf32(tmem, smem_desc(al + ks), smem_desc(bh + ks), ID, 1);
+      uint32_t r[N];
+#pragma unroll
+      for (int cc = 0; cc < N; cc += 16) {
+        uint32_t (&rr)[16] = *reinterpret_cast<uint32_t(*)[16]>(r + cc);
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + a * (uint32_t)N + (uint32_t)cc, rr);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_acce[a]));
+      const uint64_t rb = tile_base(bt) | rowoff[jrow];
+      // columns 4g..4g+3: the even lane writes 4g, 4g+1 and the odd lane
+      // 4g+2, 4g+3, each as (re, im) pairs; one shuffle per value moved
+#pragma unroll
+      for (int g = 0; g < N / 4; ++g) {
+        const float s0 = __uint_as_float(odd ? r[4 * g] : r[4 * g + 2]);
+        const float s1 = __uint_as_float(odd ? r[4 * g + 1] : r[4 * g + 3]);
+        const float t0 = __shfl_xor_sync(0xffffffffu, s0, 1);
+        const float t1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+        const int c = 4 * g + (odd ? 2 : 0);
+        float2 x0, x1;
+        if (!odd) {  // own: real parts; received: imaginary parts
+          x0 = make_float2(__uint_as_float(r[4 * g]), t0);
+          x1 = make_float2(__uint_as_float(r[4 * g + 1]), t1);
+        } else {     // own: imaginary parts; received: real parts
+          x0 = make_float2(t0, __uint_as_float(r[4 * g + 2]));
+          x1 = make_float2(t1, __uint_as_float(r[4 * g + 3]));
+        }
+        if (P.contig) {
+          *reinterpret_cast<float4*>(P.psi + (rb | (uint64_t)c)) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        } else {
+          P.psi[rb | coloff[c]] = x0;
+          P.psi[rb | coloff[c + 1]] = x1;
         }
       }
-      mma_commit(mb);
     }
-  };
-  uint64_t bt = blockIdx.x;
-  uint64_t base = 0;
-  if (bt < nb) {
-    base = tile_base(bt);
-    load_tile(base);
-    stage_and_issue();
-  }
-  for (; bt < nb; bt += gridDim.x) {
-    // loads of the next tile are in flight while this tile's MMAs finish and
-    // its accumulator drains
-    const uint64_t nxt = bt + gridDim.x;
-    uint64_t nbase = 0;
-    if (nxt < nb) {
-      nbase = tile_base(nxt);
-      load_tile(nbase);
-    }
-    const bool ok = mbar_wait(mb, parity);
-    parity ^= 1u;
-    if (!ok) abort_all = 1;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (abort_all) {
-      if (tid == 0) atomicExch(&g_tc_error, 1);
-      break;
-    }
-    {  // accumulator (row = TMEM lane) -> staging tile; warps w and w+4 share lanes
-      const int lane_base = 32 * (warp & 3);
-      const int row = lane_base + lane;
-      const int c0 = (warp >> 2) * (N / 2);
+  } else if (lane == 0) {
+    // ---- MMA issue ----
+    constexpr uint32_t ID = idesc_tf32<N>();
+    const uint32_t ah = smem_u32(Aop), al = ah + A_FLOATS * 4u;
+    uint32_t it = 0;
+    for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x, ++it) {
+      const uint32_t s = it % ST, ph = (it / ST) & 1u, a = it & 1u, pa = (it >> 1) & 1u;
+      if (!mbar_wait_or_abort(smem_u32(&bar_full[s]), ph, &abort_all) ||
+          !mbar_wait_or_abort(smem_u32(&bar_acce[a]), pa ^ 1u, &abort_all)) {
+        fail();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t bh = smem_u32(Bop + s * NOP * B_FLOATS), bl = bh + B_FLOATS * 4u;
+      const uint32_t d = tmem + a * (uint32_t)N;
 #pragma unroll 1
-      for (int cc = 0; cc < N / 2; cc += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(c0 + cc), r);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) Dsm[row * DP + c0 + cc + i] = __uint_as_float(r[i]);
+      for (int k = 0; k < kTcKR / 8; ++k) {  // K = 8 per instruction: two core matrices
+        const uint32_t ks = (uint32_t)k * 256u;
+        mma_tf32(d, smem_desc(ah + ks), smem_desc(bh + ks), ID, k > 0);
+        if (X3) {
+          mma_tf32(d, smem_desc(ah + ks), smem_desc(bl + ks), ID, 1);
+          mma_tf32(d, smem_desc(al + ks), smem_desc(bh + ks), ID, 1);
+        }
+      }
+      mma_commit(smem_u32(&bar_empty[s]));
+      mma_commit(smem_u32(&bar_accf[a]));
+    }
+    // every MMA issued above has completed before the accumulators are freed
+    mma_commit(smem_u32(&bar_fin));
+    if (!mbar_wait_or_abort(smem_u32(&bar_fin), 0, &abort_all)) {
+      // aborting: still give the tensor pipe its bounded time to finish
+      const unsigned long long t0 = global_ns();
+      for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(&bar_fin)), "r"(0u)
+            : "memory");
+        if (done || global_ns() - t0 > kWaitNs) break;
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    for (int e = tid; e < kTcDim * N; e += kTcThreads) {
-      const int c = e & (N - 1), j = e >> CB;
-      P.psi[base | rowoff[j] | coloff[c]] = make_float2(Dsm[j * DP + c], Dsm[(j + kTcDim) * DP + c]);
-    }
-    __syncthreads();  // the staging tile (B region) is free again
-    if (nxt < nb) {
-      base = nbase;
-      stage_and_issue();
-    }
   }
+  __syncwarp();  // the MMA warp's other lanes wait here for lane 0
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * N))
                  : "memory");
 }
 
-template <int CB, bool X3>
+template <int CB, bool X3, int ST>
 constexpr size_t tc_smem() {
   constexpr size_t N = size_t(1) << CB;
-  constexpr size_t a = (X3 ? 2 : 1) * size_t(kTcKR) * kTcKR * 4;
-  constexpr size_t b = (X3 ? 2 : 1) * N * kTcKR * 4;
-  constexpr size_t d = size_t(kTcKR) * (N + 1) * 4;
-  return a + (b > d ? b : d);
+  return (X3 ? 2 : 1) * (size_t(kTcKR) * kTcKR * 4 + ST * N * kTcKR * 4);
 }
 
-template <int CB, bool X3>
+template <int CB, bool X3, int ST>
 int launch_tc(const TcParams& P, cudaStream_t s) {
   static unsigned attr_done = 0;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr size_t smem = tc_smem<CB, X3>();
-  static_assert(smem <= 227u * 1024u - 4096u, "tensor-core tile exceeds shared memory");
+  constexpr size_t smem = tc_smem<CB, X3, ST>();
+  static_assert(smem <= 227u * 1024u - 2048u, "tensor-core pipeline exceeds shared memory");
   if (dev >= 32 || !((attr_done >> dev) & 1u)) {
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3>,
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 32) attr_done |= 1u << dev;
   }
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
-  const int per_sm = (2 * (smem + 4096) <= 228u * 1024u) ? 2 : 1;
-  const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms * per_sm);
-  fused_tc_kernel<CB, X3><<<(unsigned)grid, kTcThreads, smem, s>>>(P);
+  const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms);
+  fused_tc_kernel<CB, X3, ST><<<(unsigned)grid, kTcThreads2, smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error("tensor-core fused kernel launch", e);
@@ -352,11 +413,13 @@ void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out) {
   out->assign((x3 ? 2 : 1) * R * R, 0.0f);
   for (int m = 0; m < R; ++m)
     for (int kk = 0; kk < R; ++kk) {
-      const int r = m & (D - 1), c = kk & (D - 1);
+      // M index 2r + (0: real, 1: imaginary output part); K index 2c + (0:
+      // real, 1: imaginary input part)
+      const int r = m >> 1, c = kk >> 1;
       const float ur = u[2 * (r * D + c)], ui = u[2 * (r * D + c) + 1];
       float w;
-      if (m < D) w = kk < D ? ur : -ui;
-      else w = kk < D ? ui : ur;
+      if (!(m & 1)) w = (kk & 1) ? -ui : ur;
+      else w = (kk & 1) ? ur : ui;
       const float hi = tf32_round_host(w);
       const uint32_t o = core_off((uint32_t)m, (uint32_t)kk) >> 2;
       (*out)[o] = hi;
@@ -389,18 +452,21 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
     P.targets[j] = (int8_t)a.targets[j];
     P.fixed |= 1ull << a.targets[j];
   }
-  const int cb = std::min(6, a.n - kTcK);  // 64 columns per tile
+  // columns: the lowest non-target qubits; 64 per tile for TF32, 32 for
+  // 3xTF32 (its hi and lo operands double the shared memory per stage)
+  const int cb = std::min(x3 ? 5 : 6, a.n - kTcK);
   int got = 0;
   for (int q = 0; q < a.n && got < cb; ++q)
     if (!((P.fixed >> q) & 1ull)) P.cols[got++] = (int8_t)q;
   for (int j = got; j < 8; ++j) P.cols[j] = -1;
-  for (int j = 0; j < cb; ++j) P.fixed |= 1ull << P.cols[j];
-  if (x3) {
-    if (cb == 5) return launch_tc<5, true>(P, s);
-    return launch_tc<6, true>(P, s);
+  P.contig = 1;
+  for (int j = 0; j < cb; ++j) {
+    P.fixed |= 1ull << P.cols[j];
+    if (P.cols[j] != j) P.contig = 0;
   }
-  if (cb == 5) return launch_tc<5, false>(P, s);
-  return launch_tc<6, false>(P, s);
+  if (x3) return launch_tc<5, true, 2>(P, s);
+  if (cb == 5) return launch_tc<5, false, 4>(P, s);
+  return launch_tc<6, false, 4>(P, s);
 }
 
 }  // namespace qs
