@@ -246,10 +246,18 @@ def profile_run(args):
     from paper_2408_09055_gb300 import qsim as Q
     from synth import circuits as C
     n = args.profile_run
-    gates = C.mixed_circuit(n, N_GATES, SEED)
-    opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=args.shm_max)
-    if args.algo == "ordered":
-        opts.algo = Q.QS_ALGO_ORDERED
+    if args.plan.startswith("F-"):
+        gates = C.entangling_circuit(n, 8, SEED) if args.workload == "entangling" else C.mixed_circuit(n, N_GATES, SEED)
+        prec = {"F-FP32": Q.QS_PREC_FP32, "F-TF32": Q.QS_PREC_TF32, "F-TF32X3": Q.QS_PREC_TF32X3}[args.plan]
+        cost = Q.default_cost_table()
+        for k in range(16):
+            cost.fuse_cost[k] = 1.0
+        opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=prec, fuse_kmax=6, fuse_kmin=6, cost=cost)
+    else:
+        gates = C.mixed_circuit(n, N_GATES, SEED)
+        opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=args.shm_max)
+        if args.algo == "ordered":
+            opts.algo = Q.QS_ALGO_ORDERED
     plan = Q.Plan(n, gates, opts)
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     st = Q.State(n, buf.data_ptr())
@@ -388,7 +396,8 @@ def main():
     ap.add_argument("--workload", default="mixed", choices=["mixed", "entangling"])
     ap.add_argument("--profile-run", type=int, default=0, metavar="N",
                     help="plan the workload's circuit generator at N qubits and run the plan "
-                         "once, untimed (a small case for profiler captures)")
+                         "once, untimed (a small case for profiler captures); with --plan F-*, "
+                         "an 8-layer circuit with every kernel fused")
     ap.add_argument("--staged", type=int, default=0, metavar="N",
                     help="measure staged execution instead: an N-qubit state in page-locked host "
                          "memory, run chunk by chunk with --local-qubits L")

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "internal.hpp"
@@ -67,13 +68,28 @@ __host__ __device__ constexpr uint32_t idesc_tf32() {
          | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcKR >> 4) << 24);  // K-major A and B
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
+// D (+)= A B with A read from tensor memory (M = 128 lanes, K along columns)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
       :
-      : "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// 32 consecutive columns of this warp's 32 lanes, one lane per thread
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+      "%32};"
+      :
+      : "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
 }
 
@@ -148,28 +164,47 @@ constexpr int kProdWarps = 8;
 constexpr int kDrainWarps = 4;
 constexpr int kTcThreads2 = 32 * (kProdWarps + kDrainWarps + 1);
 
-template <int CB, bool X3, int ST>
+template <int CB, bool X3, int ST, bool WIDE>
 __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_constant__ TcParams P) {
+  using Off = typename std::conditional<WIDE, uint64_t, uint32_t>::type;  // amplitude offsets
   constexpr int N = 1 << CB;
   constexpr int NOP = X3 ? 2 : 1;
   constexpr uint32_t A_FLOATS = kTcKR * kTcKR;
   constexpr uint32_t B_FLOATS = N * kTcKR;
   constexpr int TASKS = (N / 8) * (kTcDim / 4);  // warp accesses per tile: 8 columns x 4 rows
   constexpr int EPT = TASKS / kProdWarps;        // per producer thread
+  // tensor memory: A (hi, then lo) in columns [0, 128*NOP), two accumulators after it
+  constexpr uint32_t ACC0 = kTcKR * NOP;
+  constexpr uint32_t TMEM_COLS = (ACC0 + 2 * N) <= 256 ? 256 : 512;
   extern __shared__ __align__(1024) float smem[];
-  float* Aop = smem;
-  float* Bop = smem + NOP * A_FLOATS;  // stage s: hi at s*NOP*B_FLOATS, lo after it
+  float* Bop = smem;  // stage s: hi at s*NOP*B_FLOATS, lo after it
   __shared__ __align__(8) uint64_t bar_full[ST], bar_empty[ST], bar_accf[2], bar_acce[2], bar_fin;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_all;
   __shared__ unsigned long long rowoff[kTcDim];
   __shared__ unsigned long long coloff[N];
+  // runs of non-fixed qubits: tile index bits [src, src+len) go to [dst, dst+len)
+  __shared__ uint8_t run_src[24], run_dst[24], run_len[24];
+  __shared__ int nruns;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  {  // unitary (host-arranged in the core layout) into shared memory
-    const float4* src = reinterpret_cast<const float4*>(P.w);
-    float4* dst = reinterpret_cast<float4*>(Aop);
-    for (uint32_t i = tid; i < NOP * A_FLOATS / 4; i += kTcThreads2) dst[i] = src[i];
+  if (tid == 0) {
+    int nr = 0, src = 0;
+    for (int q = 0; q < P.n;) {
+      if ((P.fixed >> q) & 1ull) {
+        ++q;
+        continue;
+      }
+      int len = 0;
+      while (q + len < P.n && !((P.fixed >> (q + len)) & 1ull)) ++len;
+      run_src[nr] = (uint8_t)src;
+      run_dst[nr] = (uint8_t)q;
+      run_len[nr] = (uint8_t)len;
+      ++nr;
+      src += len;
+      q += len;
+    }
+    nruns = nr;
   }
   for (int r = tid; r < kTcDim; r += kTcThreads2) {
     unsigned long long o = 0;
@@ -200,7 +235,7 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base)),
-                 "r"((uint32_t)(2 * N))
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -208,14 +243,35 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint64_t nb = 1ull << (P.n - kTcK - CB);
-  auto tile_base = [&](uint64_t bt) {
-    uint64_t base = 0, x = bt;
-    for (int q = 0; q < P.n && x; ++q)
-      if (!((P.fixed >> q) & 1ull)) {
-        base |= (x & 1ull) << q;
-        x >>= 1;
+  if (warp < 4) {  // the unitary (row m = TMEM lane m, K along columns), once per CTA
+    const int m = 32 * warp + lane;
+#pragma unroll 1
+    for (int h = 0; h < NOP; ++h)
+#pragma unroll 1
+      for (int c0 = 0; c0 < kTcKR; c0 += 32) {
+        const float4* src = reinterpret_cast<const float4*>(P.w + h * A_FLOATS + m * kTcKR + c0);
+        uint32_t r[32];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float4 x = src[i];
+          r[4 * i] = __float_as_uint(x.x);
+          r[4 * i + 1] = __float_as_uint(x.y);
+          r[4 * i + 2] = __float_as_uint(x.z);
+          r[4 * i + 3] = __float_as_uint(x.w);
+        }
+        tmem_st32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(h * kTcKR + c0), r);
       }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint64_t nb = 1ull << (P.n - kTcK - CB);
+  const int nr = nruns;
+  auto tile_base = [&](uint64_t bt) {
+    uint64_t base = 0;
+    for (int r = 0; r < nr; ++r)
+      base |= ((bt >> run_src[r]) & ((1ull << run_len[r]) - 1ull)) << run_dst[r];
     return base;
   };
   auto fail = [&]() {
@@ -225,42 +281,73 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
 
   if (warp < kProdWarps) {
     // ---- producers ----
-    float2 cur[EPT], nxt[EPT];
-    auto load = [&](uint64_t bt, float2 (&v)[EPT]) {
-      const uint64_t base = tile_base(bt);
+    // two register buffers alternate, so the loads of the tile after next
+    // are in flight while this tile is rounded and stored
+    float2 va[EPT], vb[EPT];
+    Off goff[EPT];       // element offsets inside a tile (the same for every tile)
+    uint32_t soff[EPT];  // and their operand positions (floats)
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int task = warp + kProdWarps * e;
-        const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
-        v[e] = P.psi[base | rowoff[j] | coloff[c]];
-      }
+    for (int e = 0; e < EPT; ++e) {
+      const int task = warp + kProdWarps * e;
+      const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
+      goff[e] = (Off)(rowoff[j] | coloff[c]);
+      soff[e] = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
+    }
+    auto load = [&](uint64_t bt, float2 (&v)[EPT]) {
+      const float2* src = P.psi + tile_base(bt);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[e] = src[goff[e]];
     };
-    uint32_t it = 0;
-    uint64_t bt = blockIdx.x;
-    if (bt < nb) load(bt, cur);
-    for (; bt < nb; bt += gridDim.x, ++it) {
-      const uint64_t bn = bt + gridDim.x;
-      if (bn < nb) load(bn, nxt);
+    // waits for stage `it`'s buffer, stores tile v into it; false to stop
+    auto put = [&](uint32_t it, const float2 (&v)[EPT]) {
       const uint32_t s = it % ST, ph = (it / ST) & 1u;
       const bool ok = mbar_wait_or_abort(smem_u32(&bar_empty[s]), ph ^ 1u, &abort_all);
       if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together
         fail();
-        break;
+        return false;
       }
       float* bh = Bop + s * NOP * B_FLOATS;
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
-        const int task = warp + kProdWarps * e;
-        const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
-        const uint32_t o = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
-        const float hr = tf32_rna(cur[e].x), hi = tf32_rna(cur[e].y);
-        *reinterpret_cast<float2*>(bh + o) = make_float2(hr, hi);
-        if (X3) *reinterpret_cast<float2*>(bh + B_FLOATS + o) = make_float2(cur[e].x - hr, cur[e].y - hi);
+        const float hr = tf32_rna(v[e].x), hi = tf32_rna(v[e].y);
+        *reinterpret_cast<float2*>(bh + soff[e]) = make_float2(hr, hi);
+        if (X3) *reinterpret_cast<float2*>(bh + B_FLOATS + soff[e]) = make_float2(v[e].x - hr, v[e].y - hi);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&bar_full[s]));
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) cur[e] = nxt[e];
+      return true;
+    };
+    // rows of the tile three ahead go to L2 with bulk prefetches (one row
+    // of N contiguous amplitudes per lane 0..7 of each producer warp), so
+    // the register loads above mostly hit L2
+    constexpr int kPf = 3;
+    const bool pf = P.contig && lane < 8;
+    const int pf_row = warp * 8 + lane;
+    auto prefetch = [&](uint64_t bt) {
+      if (pf && bt < nb) {
+        const float2* row = P.psi + (tile_base(bt) | rowoff[pf_row]);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row), "r"((uint32_t)(N * 8))
+                     : "memory");
+      }
+    };
+    const uint64_t g = gridDim.x;
+    uint64_t bt = blockIdx.x;
+    uint32_t it = 0;
+    for (int k = 2; k < kPf; ++k) prefetch(bt + k * g);
+    if (bt < nb) load(bt, va);
+    if (bt + g < nb) load(bt + g, vb);
+    while (bt < nb) {
+      prefetch(bt + kPf * g);
+      if (!put(it, va)) break;
+      ++it;
+      bt += g;
+      if (bt + g < nb) load(bt + g, va);
+      if (bt >= nb) break;
+      prefetch(bt + kPf * g);
+      if (!put(it, vb)) break;
+      ++it;
+      bt += g;
+      if (bt + g < nb) load(bt + g, vb);
     }
   } else if (warp < kProdWarps + kDrainWarps) {
     // ---- drain ----
@@ -280,7 +367,7 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
 #pragma unroll
       for (int cc = 0; cc < N; cc += 16) {
         uint32_t (&rr)[16] = *reinterpret_cast<uint32_t(*)[16]>(r + cc);
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + a * (uint32_t)N + (uint32_t)cc, rr);
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + ACC0 + a * (uint32_t)N + (uint32_t)cc, rr);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(smem_u32(&bar_acce[a]));
@@ -313,7 +400,6 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
   } else if (lane == 0) {
     // ---- MMA issue ----
     constexpr uint32_t ID = idesc_tf32<N>();
-    const uint32_t ah = smem_u32(Aop), al = ah + A_FLOATS * 4u;
     uint32_t it = 0;
     for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x, ++it) {
       const uint32_t s = it % ST, ph = (it / ST) & 1u, a = it & 1u, pa = (it >> 1) & 1u;
@@ -324,14 +410,18 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t bh = smem_u32(Bop + s * NOP * B_FLOATS), bl = bh + B_FLOATS * 4u;
-      const uint32_t d = tmem + a * (uint32_t)N;
+      const uint32_t d = tmem + ACC0 + a * (uint32_t)N;
+      // a K step of 8: 8 TMEM columns of A; 256 bytes of B (+16 in the
+      // descriptor's address field)
+      const uint64_t dbh = smem_desc(bh), dbl = smem_desc(bl);
 #pragma unroll 1
-      for (int k = 0; k < kTcKR / 8; ++k) {  // K = 8 per instruction: two core matrices
-        const uint32_t ks = (uint32_t)k * 256u;
-        mma_tf32(d, smem_desc(ah + ks), smem_desc(bh + ks), ID, k > 0);
+      for (int k = 0; k < kTcKR / 8; ++k) {
+        const uint64_t ks = (uint64_t)k * 16u;
+        const uint32_t ka = tmem + 8u * (uint32_t)k;
+        mma_tf32_ta(d, ka, dbh + ks, ID, k > 0);
         if (X3) {
-          mma_tf32(d, smem_desc(ah + ks), smem_desc(bl + ks), ID, 1);
-          mma_tf32(d, smem_desc(al + ks), smem_desc(bh + ks), ID, 1);
+          mma_tf32_ta(d, ka, dbl + ks, ID, 1);
+          mma_tf32_ta(d, ka + kTcKR, dbh + ks, ID, 1);
         }
       }
       mma_commit(smem_u32(&bar_empty[s]));
@@ -359,17 +449,17 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * N))
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                  : "memory");
 }
 
 template <int CB, bool X3, int ST>
 constexpr size_t tc_smem() {
   constexpr size_t N = size_t(1) << CB;
-  return (X3 ? 2 : 1) * (size_t(kTcKR) * kTcKR * 4 + ST * N * kTcKR * 4);
+  return (X3 ? 2 : 1) * ST * N * kTcKR * 4;  // the operand ring; the unitary lives in TMEM
 }
 
-template <int CB, bool X3, int ST>
+template <int CB, bool X3, int ST, bool WIDE>
 int launch_tc(const TcParams& P, cudaStream_t s) {
   static unsigned attr_done = 0;
   int dev = 0, sms = 148;
@@ -378,14 +468,14 @@ int launch_tc(const TcParams& P, cudaStream_t s) {
   constexpr size_t smem = tc_smem<CB, X3, ST>();
   static_assert(smem <= 227u * 1024u - 2048u, "tensor-core pipeline exceeds shared memory");
   if (dev >= 32 || !((attr_done >> dev) & 1u)) {
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST>,
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 32) attr_done |= 1u << dev;
   }
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms);
-  fused_tc_kernel<CB, X3, ST><<<(unsigned)grid, kTcThreads2, smem, s>>>(P);
+  fused_tc_kernel<CB, X3, ST, WIDE><<<(unsigned)grid, kTcThreads2, smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error("tensor-core fused kernel launch", e);
@@ -406,8 +496,8 @@ float tf32_round_host(float x) {
 
 }  // namespace
 
-// W for a 2^6 x 2^6 complex unitary (row-major complex64), arranged in the
-// kernel's shared-memory layout: hi part, then (3xTF32) lo part.
+// W for a 2^6 x 2^6 complex unitary (row-major complex64) as the kernel's
+// tensor-memory A operand: 128 x 128 row-major, hi part, then (3xTF32) lo.
 void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out) {
   const int D = kTcDim, R = kTcKR;
   out->assign((x3 ? 2 : 1) * R * R, 0.0f);
@@ -421,7 +511,7 @@ void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out) {
       if (!(m & 1)) w = (kk & 1) ? -ui : ur;
       else w = (kk & 1) ? ur : ui;
       const float hi = tf32_round_host(w);
-      const uint32_t o = core_off((uint32_t)m, (uint32_t)kk) >> 2;
+      const uint32_t o = (uint32_t)(m * R + kk);  // row-major: row m goes to TMEM lane m
       (*out)[o] = hi;
       if (x3) (*out)[R * R + o] = tf32_round_host(w - hi);
     }
@@ -452,9 +542,8 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
     P.targets[j] = (int8_t)a.targets[j];
     P.fixed |= 1ull << a.targets[j];
   }
-  // columns: the lowest non-target qubits; 64 per tile for TF32, 32 for
-  // 3xTF32 (its hi and lo operands double the shared memory per stage)
-  const int cb = std::min(x3 ? 5 : 6, a.n - kTcK);
+  // columns: the 64 lowest non-target qubits (32 when n = 11)
+  const int cb = std::min(6, a.n - kTcK);
   int got = 0;
   for (int q = 0; q < a.n && got < cb; ++q)
     if (!((P.fixed >> q) & 1ull)) P.cols[got++] = (int8_t)q;
@@ -464,9 +553,12 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
     P.fixed |= 1ull << P.cols[j];
     if (P.cols[j] != j) P.contig = 0;
   }
-  if (x3) return launch_tc<5, true, 2>(P, s);
-  if (cb == 5) return launch_tc<5, false, 4>(P, s);
-  return launch_tc<6, false, 4>(P, s);
+  if (a.n > 32) {  // amplitude offsets need 64 bits
+    if (x3) return launch_tc<6, true, 3, true>(P, s);
+    return launch_tc<6, false, 6, true>(P, s);
+  }
+  if (x3) return cb == 5 ? launch_tc<5, true, 3, false>(P, s) : launch_tc<6, true, 3, false>(P, s);
+  return cb == 5 ? launch_tc<5, false, 6, false>(P, s) : launch_tc<6, false, 6, false>(P, s);
 }
 
 }  // namespace qs
