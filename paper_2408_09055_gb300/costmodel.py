@@ -4,9 +4,11 @@ training with the library's own kernels, save/load.
 Every sample is one kernel of the kind the planners emit, timed as the
 library executes it on a resident 30-qubit state:
 
-* shared-memory samples: a random subcircuit (an active set of 1..10 of the
-  30 qubits, 1..64 gates of the mixed gate set inside it), planned as a single
-  shared-memory kernel and compiled to its specialised form;
+* shared-memory samples: a random subcircuit (an active set of 1..13 of the
+  30 qubits -- the planner's range -- and 1..64 gates inside it, drawn from
+  the mixed-circuit gate set or, for every other sample, from all ten gate
+  types), planned as a single shared-memory kernel and compiled to its
+  specialised form;
 * fused samples: a random subcircuit on 1..6 qubits applied as one fused
   unitary in the requested precision.
 
@@ -33,21 +35,22 @@ MODEL_PATH = os.path.join(PKG, "data", "costmodel_gb300.npz")
 N_REF = 30  # state size the timings are taken on
 
 
-def _sample_specs(n, count, seed, fused_fraction, precision):
+def _sample_specs(n, count, seed, fused_fraction, precision, max_active=13):
     from synth import circuits as C
     rng = np.random.default_rng(seed)
     specs = []
     for i in range(count):
         sub_seed = int(rng.integers(0, 2 ** 62))
         fused = rng.uniform() < fused_fraction
+        gate_set = C.ALL_TYPES if i % 2 else C.MIXED_SET
         if fused:
-            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=6)
+            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=6, gate_set=gate_set)
             cost = Q.default_cost_table()
             for k in range(16):
                 cost.fuse_cost[k] = 1.0
             opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=6, precision=precision, cost=cost)
         else:
-            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=10)
+            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=max_active, gate_set=gate_set)
             opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=0, shm_max_active=14)
         specs.append((g, opts, opts.cost))
     return specs
@@ -61,12 +64,12 @@ def _build(n, spec):
     return plan
 
 
-def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.2, precision=Q.QS_PREC_TF32X3,
-             reps=3, batch=256, threads=None, stream=None, log=print):
+def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.25, precision=Q.QS_PREC_TF32X3,
+             reps=3, batch=256, threads=None, stream=None, log=print, max_active=13):
     """Times `count` random kernels; returns (X [count x F], y = ln(us), meta)."""
     import torch
     threads = threads or os.cpu_count() or 4
-    specs = _sample_specs(n, count, seed, fused_fraction, precision)
+    specs = _sample_specs(n, count, seed, fused_fraction, precision, max_active)
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     st = Q.State(n, buf.data_ptr())
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
@@ -93,7 +96,7 @@ def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.2, precision=Q.QS_PRE
             del plans
             if log:
                 log(f"timed {min(b0 + batch, len(specs))}/{len(specs)} kernels, {time.time() - t0:.0f} s")
-    meta = {"n": n, "count": len(y), "seed": seed, "fused_fraction": fused_fraction,
+    meta = {"n": n, "count": len(y), "seed": seed, "fused_fraction": fused_fraction, "max_active": max_active,
             "precision": int(precision), "reps": reps, "seconds": time.time() - t0,
             "fused_samples": int(sum(1 for k in kinds if k == Q.QS_KERNEL_FUSED))}
     return np.asarray(X, dtype=np.float32), np.asarray(y, dtype=np.float32), meta
@@ -181,7 +184,7 @@ def main(argv=None):
     dataset beside it."""
     import argparse
     ap = argparse.ArgumentParser()
-    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--count", type=int, default=6144)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--out", default=MODEL_PATH)

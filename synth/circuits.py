@@ -45,6 +45,7 @@ NAMES = ["H", "X", "RX", "RZ", "U3", "CX", "CZ", "CP", "SWAP", "RXX"]
 NQ = [1, 1, 1, 1, 1, 2, 2, 2, 2, 2]
 NPARAM = [0, 0, 1, 1, 3, 0, 0, 1, 0, 1]
 MIXED_SET = [H, X, RX, RZ, CX, CZ, CP, SWAP]
+ALL_TYPES = list(range(10))
 
 GATE_DTYPE = np.dtype(
     {
@@ -136,24 +137,25 @@ def entangling_circuit(n: int = 32, layers: int = 40, seed: int = 0) -> np.ndarr
 
 
 def random_subcircuit(n: int = 30, seed: int = 0, max_active: int = 10,
-                      max_gates: int = 64):
-    """One cost-model sample: (gates, sorted active qubit list)."""
+                      max_gates: int = 64, gate_set=None):
+    """One cost-model sample: (gates, sorted active qubit list).  Gate types
+    are drawn uniformly from `gate_set` (default: the mixed-circuit set)."""
     rng = np.random.default_rng(seed)
     na = int(rng.integers(1, max_active + 1))
     act = sorted(int(x) for x in rng.choice(n, size=na, replace=False))
     ng = int(rng.integers(1, max_gates + 1))
-    types = MIXED_SET if na >= 2 else [t for t in MIXED_SET if NQ[t] == 1]
+    pool = MIXED_SET if gate_set is None else list(gate_set)
+    types = pool if na >= 2 else [t for t in pool if NQ[t] == 1]
     items = []
     for _ in range(ng):
         t = types[int(rng.integers(0, len(types)))]
+        th = [float(x) for x in _angles(rng, NPARAM[t])] if NPARAM[t] else []
         if NQ[t] == 2:
             a, b = rng.choice(na, size=2, replace=False)
-            th = float(_angles(rng, 1)[0]) if t == CP else 0.0
-            items.append((t, act[int(a)], act[int(b)], th))
+            items.append((t, act[int(a)], act[int(b)], *th))
         else:
             q = act[int(rng.integers(0, na))]
-            th = float(_angles(rng, 1)[0]) if t in (RX, RZ) else 0.0
-            items.append((t, q, None, th))
+            items.append((t, q, None, *th))
     return make_gates(items), act
 
 
