@@ -10,7 +10,12 @@ library executes it on a resident 30-qubit state:
   types), planned as a single shared-memory kernel and compiled to its
   specialised form;
 * fused samples: a random subcircuit on 1..6 qubits applied as one fused
-  unitary in the requested precision.
+  unitary in the requested precision;
+* planner-shaped samples (a fraction of the count): kernels of analytic
+  Kernelize plans of freshly seeded 30-qubit mixed and entangling circuits
+  (seeds distinct from any benchmark seed), each timed alone -- the kernels
+  the planner actually weighs, which random subcircuits rarely resemble
+  (dozens of dense gates on 11..14 qubits).
 
 Features come from ``qs_kernel_features`` of the kernel as planned; the
 target is ln(microseconds).  Training runs ``qs_mlp_train_step`` (the
@@ -56,6 +61,32 @@ def _sample_specs(n, count, seed, fused_fraction, precision, max_active=13):
     return specs
 
 
+def _workload_specs(n, count, seed):
+    """Kernels of analytic Kernelize plans of seeded workload circuits, as
+    single-kernel specs (greedy packing of the kernel's gates, which keeps
+    them in one shared-memory kernel)."""
+    from synth import circuits as C
+    rng = np.random.default_rng(seed + 7919)
+    specs = []
+    while len(specs) < count:
+        wseed = 10_000 + int(rng.integers(0, 1 << 30))
+        if rng.uniform() < 0.5:
+            g = C.mixed_circuit(n, 1200, wseed)
+        else:
+            g = C.entangling_circuit(n, 10, wseed)
+        smax = int(rng.integers(11, 15))
+        plan = Q.Plan(n, g, Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=smax,
+                                           shm_variant=2))
+        nk = plan.stats().num_kernels
+        for k in rng.permutation(nk)[:max(1, nk // 4)]:
+            sub = g[plan.kernel_gates(int(k))]
+            opts = Q.default_opts(algo=Q.QS_ALGO_GREEDY, fuse_kmax=0, shm_max_active=14)
+            specs.append((sub, opts, opts.cost))
+            if len(specs) >= count:
+                break
+    return specs
+
+
 def _build(n, spec):
     g, opts, _keep = spec
     plan = Q.Plan(n, g, opts)
@@ -65,11 +96,14 @@ def _build(n, spec):
 
 
 def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.25, precision=Q.QS_PREC_TF32X3,
-             reps=3, batch=256, threads=None, stream=None, log=print, max_active=13):
+             reps=3, batch=256, threads=None, stream=None, log=print, max_active=13,
+             workload_fraction=0.2):
     """Times `count` random kernels; returns (X [count x F], y = ln(us), meta)."""
     import torch
     threads = threads or os.cpu_count() or 4
-    specs = _sample_specs(n, count, seed, fused_fraction, precision, max_active)
+    nw = int(round(workload_fraction * count))
+    specs = _sample_specs(n, count - nw, seed, fused_fraction, precision, max_active)
+    specs += _workload_specs(n, nw, seed)
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     st = Q.State(n, buf.data_ptr())
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
@@ -97,6 +131,7 @@ def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.25, precision=Q.QS_PR
             if log:
                 log(f"timed {min(b0 + batch, len(specs))}/{len(specs)} kernels, {time.time() - t0:.0f} s")
     meta = {"n": n, "count": len(y), "seed": seed, "fused_fraction": fused_fraction, "max_active": max_active,
+            "workload_fraction": workload_fraction,
             "precision": int(precision), "reps": reps, "seconds": time.time() - t0,
             "fused_samples": int(sum(1 for k in kinds if k == Q.QS_KERNEL_FUSED))}
     return np.asarray(X, dtype=np.float32), np.asarray(y, dtype=np.float32), meta
