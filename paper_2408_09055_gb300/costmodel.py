@@ -108,11 +108,23 @@ def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.25, precision=Q.QS_PR
     st = Q.State(n, buf.data_ptr())
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     st.set_zero(s)
-    X, y, kinds = [], [], []
     t0 = time.time()
+    X, y, kinds = _time_specs(n, specs, reps, st, s, threads)
+    if log:
+        log(f"timed {len(y)} kernels in {time.time() - t0:.0f} s")
+    meta = {"n": n, "count": len(y), "seed": seed, "fused_fraction": fused_fraction, "max_active": max_active,
+            "workload_fraction": workload_fraction,
+            "precision": int(precision), "reps": reps, "seconds": time.time() - t0,
+            "fused_samples": int(sum(1 for k in kinds if k == Q.QS_KERNEL_FUSED))}
+    return np.asarray(X, dtype=np.float32), np.asarray(y, dtype=np.float32), meta
+
+
+def _time_specs(n, specs, reps, st, s, threads, log=None):
+    """Plans every spec as one kernel and times it; returns (X, y, kinds)."""
+    X, y, kinds = [], [], []
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        for b0 in range(0, len(specs), batch):
-            part = specs[b0:b0 + batch]
+        for b0 in range(0, len(specs), 256):
+            part = specs[b0:b0 + 256]
             plans = list(ex.map(lambda sp: _build(n, sp), part))
             for sp, plan in zip(part, plans):
                 if plan is None:
@@ -128,13 +140,50 @@ def generate(n=N_REF, count=4096, seed=0, fused_fraction=0.25, precision=Q.QS_PR
                 y.append(math.log(ms[0] / runs * 1e3))
                 kinds.append(d.type)
             del plans
-            if log:
-                log(f"timed {min(b0 + batch, len(specs))}/{len(specs)} kernels, {time.time() - t0:.0f} s")
-    meta = {"n": n, "count": len(y), "seed": seed, "fused_fraction": fused_fraction, "max_active": max_active,
-            "workload_fraction": workload_fraction,
-            "precision": int(precision), "reps": reps, "seconds": time.time() - t0,
-            "fused_samples": int(sum(1 for k in kinds if k == Q.QS_KERNEL_FUSED))}
-    return np.asarray(X, dtype=np.float32), np.asarray(y, dtype=np.float32), meta
+    return X, y, kinds
+
+
+def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC_TF32X3, reps=3,
+           epochs=300, threads=None, log=print):
+    """Active refinement: plan freshly seeded workload circuits with the
+    learned cost (Kernelize, fused kernels in `precision`), time exactly the
+    kernels those plans chose, add them to the data and retrain.  A planner
+    that minimises a learned cost steers towards kernels the model
+    underestimates; timing its own choices corrects those regions."""
+    import torch
+    from synth import circuits as C
+    threads = threads or os.cpu_count() or 4
+    rng = np.random.default_rng(seed + 104729)
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    st = Q.State(n, buf.data_ptr())
+    s = torch.cuda.current_stream().cuda_stream
+    st.set_zero(s)
+    fcost = Q.default_cost_table()
+    for k in range(16):
+        fcost.fuse_cost[k] = 1.0
+    metrics = {}
+    for r in range(rounds):
+        specs = []
+        for c in range(circuits):
+            wseed = 20_000 + int(rng.integers(0, 1 << 30))
+            g = C.mixed_circuit(n, 1200, wseed) if c % 2 else C.entangling_circuit(n, 10, wseed)
+            plan = Q.Plan(n, g, Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=precision, fuse_kmax=6,
+                                               mlp=net, shm_variant=2))
+            for k in range(plan.stats().num_kernels):
+                sub = g[plan.kernel_gates(k)]
+                if plan.kernel(k).type == Q.QS_KERNEL_FUSED:
+                    opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=6, precision=precision, cost=fcost)
+                else:
+                    opts = Q.default_opts(algo=Q.QS_ALGO_GREEDY, fuse_kmax=0, shm_max_active=14)
+                specs.append((sub, opts, opts.cost))
+        Xn, yn, kinds = _time_specs(n, specs, reps, st, s, threads)
+        X = np.concatenate([X, np.asarray(Xn, dtype=np.float32)])
+        y = np.concatenate([y, np.asarray(yn, dtype=np.float32)])
+        net, metrics = train(X, y, epochs=epochs, seed=seed)
+        if log:
+            log(f"refinement round {r + 1}: +{len(yn)} kernels ({sum(kinds)} fused), "
+                f"test mean rel err {metrics['test']['mean_rel_err']:.3f}")
+    return net, X, y, metrics
 
 
 def split(count, seed=0, fractions=(0.8, 0.1, 0.1)):
@@ -223,10 +272,15 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--out", default=MODEL_PATH)
+    ap.add_argument("--refine-rounds", type=int, default=3)
     a = ap.parse_args(argv)
     X, y, meta = generate(count=a.count, seed=a.seed)
-    np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, meta=json.dumps(meta))
     net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print)
+    if a.refine_rounds:
+        net, X, y, metrics = refine(net, X, y, rounds=a.refine_rounds, seed=a.seed, epochs=a.epochs)
+        meta["refine_rounds"] = a.refine_rounds
+        meta["count"] = int(len(y))
+    np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, meta=json.dumps(meta))
     meta["metrics"] = metrics
     save(net, a.out, meta)
     print(json.dumps(meta))
