@@ -159,14 +159,33 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parit
 //                shared-memory stages;
 //   warps 8..11  drain: TMEM accumulator -> registers -> global (one warp
 //                per TMEM lane quadrant);
-//   warp 12      one thread issues the MMAs into two TMEM accumulators.
+//   warp 12      one thread issues the MMAs into two TMEM accumulators;
+//   warp 13      (BULK) loader: each tile row -- the N column qubits are the
+//                lowest qubits, so a row is N contiguous amplitudes -- is one
+//                cp.async.bulk into a ring of RS raw stages (rows padded to
+//                keep the producers' reads conflict-free); the producers then
+//                read the raw stage instead of global memory, and no register
+//                holds data in flight.
 constexpr int kProdWarps = 8;
 constexpr int kDrainWarps = 4;
-constexpr int kTcThreads2 = 32 * (kProdWarps + kDrainWarps + 1);
+constexpr int kTcThreads2 = 32 * (kProdWarps + kDrainWarps + 1);  // + one loader warp with BULK
 
-template <int CB, bool X3, int ST, bool WIDE>
-__global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_constant__ TcParams P) {
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// one contiguous global run into shared memory, completing on an mbarrier
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+template <int CB, bool X3, int ST, bool WIDE, bool BULK, int RS>
+__global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __grid_constant__ TcParams P) {
   using Off = typename std::conditional<WIDE, uint64_t, uint32_t>::type;  // amplitude offsets
+  constexpr int RAW_PITCH = (1 << CB) + 8;      // float2 per raw row (64 B of padding)
+  constexpr int RAW_STAGE = kTcDim * RAW_PITCH;  // float2 per raw stage
   constexpr int N = 1 << CB;
   constexpr int NOP = X3 ? 2 : 1;
   constexpr uint32_t A_FLOATS = kTcKR * kTcKR;
@@ -178,7 +197,9 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
   constexpr uint32_t TMEM_COLS = (ACC0 + 2 * N) <= 256 ? 256 : 512;
   extern __shared__ __align__(1024) float smem[];
   float* Bop = smem;  // stage s: hi at s*NOP*B_FLOATS, lo after it
+  float2* Raw = reinterpret_cast<float2*>(smem + ST * NOP * B_FLOATS);  // BULK raw ring
   __shared__ __align__(8) uint64_t bar_full[ST], bar_empty[ST], bar_accf[2], bar_acce[2], bar_fin;
+  __shared__ __align__(8) uint64_t bar_rfull[RS], bar_rempty[RS];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_all;
   __shared__ unsigned long long rowoff[kTcDim];
@@ -230,6 +251,11 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
                    "r"(32 * kDrainWarps) : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_fin)) : "memory");
+    for (int r = 0; r < RS; ++r) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_rfull[r])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_rempty[r])),
+                   "r"(32 * kProdWarps) : "memory");
+    }
     abort_all = 0;
   }
   if (warp == 0) {
@@ -279,7 +305,75 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
     atomicExch(&g_tc_error, 1);
   };
 
-  if (warp < kProdWarps) {
+  if (BULK && warp < kProdWarps) {
+    // ---- producers reading the raw ring ----
+    uint32_t roff[EPT], soff[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int task = warp + kProdWarps * e;
+      const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
+      roff[e] = (uint32_t)(j * RAW_PITCH + c);
+      soff[e] = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
+    }
+    uint32_t it = 0;
+    for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x, ++it) {
+      const uint32_t r = it % RS, pr = (it / RS) & 1u, s = it % ST, ps = (it / ST) & 1u;
+      bool ok = mbar_wait_or_abort(smem_u32(&bar_rfull[r]), pr, &abort_all);
+      if (ok) ok = mbar_wait_or_abort(smem_u32(&bar_empty[s]), ps ^ 1u, &abort_all);
+      if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together
+        fail();
+        break;
+      }
+      const float2* raw = Raw + r * RAW_STAGE;
+      float2 v[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[e] = raw[roff[e]];
+      mbar_arrive(smem_u32(&bar_rempty[r]));  // the raw stage is read
+      float* bh = Bop + s * NOP * B_FLOATS;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const float hr = tf32_rna(v[e].x), hi = tf32_rna(v[e].y);
+        *reinterpret_cast<float2*>(bh + soff[e]) = make_float2(hr, hi);
+        if (X3) *reinterpret_cast<float2*>(bh + B_FLOATS + soff[e]) = make_float2(v[e].x - hr, v[e].y - hi);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_full[s]));
+    }
+  } else if (BULK && warp == kProdWarps + kDrainWarps + 1) {
+    // ---- loader ----
+    uint32_t it = 0;
+    for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x, ++it) {
+      const uint32_t r = it % RS, pr = (it / RS) & 1u;
+      const bool ok = mbar_wait_or_abort(smem_u32(&bar_rempty[r]), pr ^ 1u, &abort_all);
+      if (!__all_sync(0xffffffffu, ok)) {
+        fail();
+        break;
+      }
+      const uint32_t full = smem_u32(&bar_rfull[r]);
+      if (lane == 0) mbar_expect_tx(full, (uint32_t)(kTcDim * N * 8));
+      __syncwarp();
+      const uint64_t base = tile_base(bt);
+      const uint32_t dst = smem_u32(Raw + r * RAW_STAGE);
+      for (int row = lane; row < kTcDim; row += 32)
+        bulk_load(dst + (uint32_t)(row * RAW_PITCH * 8), P.psi + (base | rowoff[row]), (uint32_t)(N * 8), full);
+    }
+    // copies still in flight after an abort complete before the CTA exits
+    if (lane == 0)
+      for (uint32_t k = it > (uint32_t)RS ? it - RS : 0; k < it; ++k) {
+        const uint32_t r = k % RS, pr = (k / RS) & 1u;
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+          uint32_t done;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+              "selp.u32 %0, 1, 0, p;\n\t}\n"
+              : "=r"(done)
+              : "r"(smem_u32(&bar_rfull[r])), "r"(pr)
+              : "memory");
+          if (done || global_ns() - t0 > kWaitNs) break;
+        }
+      }
+  } else if (!BULK && warp < kProdWarps) {
     // ---- producers ----
     // two register buffers alternate, so the loads of the tile after next
     // are in flight while this tile is rounded and stored
@@ -453,29 +547,30 @@ __global__ void __launch_bounds__(kTcThreads2, 1) fused_tc_kernel(const __grid_c
                  : "memory");
 }
 
-template <int CB, bool X3, int ST>
+template <int CB, bool X3, int ST, bool BULK, int RS>
 constexpr size_t tc_smem() {
   constexpr size_t N = size_t(1) << CB;
-  return (X3 ? 2 : 1) * ST * N * kTcKR * 4;  // the operand ring; the unitary lives in TMEM
+  // the operand ring (the unitary lives in TMEM), plus the raw ring with BULK
+  return (X3 ? 2 : 1) * ST * N * kTcKR * 4 + (BULK ? RS * size_t(kTcDim) * (N + 8) * 8 : 0);
 }
 
-template <int CB, bool X3, int ST, bool WIDE>
+template <int CB, bool X3, int ST, bool WIDE, bool BULK = false, int RS = 1>
 int launch_tc(const TcParams& P, cudaStream_t s) {
   static unsigned attr_done = 0;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr size_t smem = tc_smem<CB, X3, ST>();
+  constexpr size_t smem = tc_smem<CB, X3, ST, BULK, RS>();
   static_assert(smem <= 227u * 1024u - 2048u, "tensor-core pipeline exceeds shared memory");
   if (dev >= 32 || !((attr_done >> dev) & 1u)) {
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE>,
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 32) attr_done |= 1u << dev;
   }
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms);
-  fused_tc_kernel<CB, X3, ST, WIDE><<<(unsigned)grid, kTcThreads2, smem, s>>>(P);
+  fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS><<<(unsigned)grid, kTcThreads2 + (BULK ? 32 : 0), smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error("tensor-core fused kernel launch", e);
@@ -556,6 +651,10 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
   if (a.n > 32) {  // amplitude offsets need 64 bits
     if (x3) return launch_tc<6, true, 3, true>(P, s);
     return launch_tc<6, false, 6, true>(P, s);
+  }
+  if (P.contig && cb == 6) {  // tile rows are contiguous: bulk-staged loads
+    if (x3) return launch_tc<6, true, 2, false, true, 2>(P, s);
+    return launch_tc<6, false, 3, false, true, 3>(P, s);
   }
   if (x3) return cb == 5 ? launch_tc<5, true, 3, false>(P, s) : launch_tc<6, true, 3, false>(P, s);
   return cb == 5 ? launch_tc<5, false, 6, false>(P, s) : launch_tc<6, false, 6, false>(P, s);

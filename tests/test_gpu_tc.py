@@ -18,9 +18,12 @@ def _apply(n, targets, u, precision, psi0):
     return buf.cpu().numpy().view(np.complex64).astype(np.complex128)
 
 
-def _case(n, k, seed):
+def _case(n, k, seed, high=False):
     rng = np.random.default_rng(seed)
-    targets = [int(t) for t in rng.permutation(n)[:k]]
+    # high: targets among qubits >= 6, so a tile's columns are the 64 lowest
+    # qubits (contiguous rows: the bulk-staged load path)
+    pool = np.arange(6, n) if high else np.arange(n)
+    targets = [int(t) for t in rng.permutation(pool)[:k]]
     sub = C.entangling_circuit(k, 3, seed) if k >= 2 else C.make_gates([(C.U3, 0, None, 0.4, 0.5, 0.6)])
     u = sim.kernel_unitary(sub, list(range(k)))
     g = sub.copy()
@@ -39,6 +42,19 @@ def test_tf32x3_meets_fp32_accuracy(n, k):
     targets, u, psi0, ref = _case(n, k, 10 * n + k)
     got = _apply(n, targets, u, Q.QS_PREC_TF32X3, psi0)
     assert_close_state(got, ref)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("n", [12, 13, 18])
+def test_contiguous_tile_rows_bulk_path(n, precision):
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    targets, u, psi0, ref = _case(n, 6, 7 * n + precision, high=True)
+    got = _apply(n, targets, u, precision, psi0)
+    if precision == Q.QS_PREC_TF32X3:
+        assert_close_state(got, ref)
+    else:
+        assert fidelity(ref, got) > 1 - 1e-4
 
 
 @pytest.mark.parametrize("n", [12, 17])
