@@ -294,10 +294,16 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
   const int nr = nruns;
+  const int nbl = P.n - kTcK - CB;  // tile index bits
+  // Tiles are visited in bit-reversed order: the CTAs working at the same
+  // time hold tiles that differ in their highest index bits, so their rows
+  // spread over the whole state instead of one narrow window per row (rows
+  // 2^t apart otherwise land in the same few memory channels).
   auto tile_base = [&](uint64_t bt) {
+    const uint64_t x = nbl ? (__brevll(bt) >> (64 - nbl)) : 0;
     uint64_t base = 0;
     for (int r = 0; r < nr; ++r)
-      base |= ((bt >> run_src[r]) & ((1ull << run_len[r]) - 1ull)) << run_dst[r];
+      base |= ((x >> run_src[r]) & ((1ull << run_len[r]) - 1ull)) << run_dst[r];
     return base;
   };
   auto fail = [&]() {
@@ -411,33 +417,17 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
       mbar_arrive(smem_u32(&bar_full[s]));
       return true;
     };
-    // rows of the tile three ahead go to L2 with bulk prefetches (one row
-    // of N contiguous amplitudes per lane 0..7 of each producer warp), so
-    // the register loads above mostly hit L2
-    constexpr int kPf = 3;
-    const bool pf = P.contig && lane < 8;
-    const int pf_row = warp * 8 + lane;
-    auto prefetch = [&](uint64_t bt) {
-      if (pf && bt < nb) {
-        const float2* row = P.psi + (tile_base(bt) | rowoff[pf_row]);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row), "r"((uint32_t)(N * 8))
-                     : "memory");
-      }
-    };
     const uint64_t g = gridDim.x;
     uint64_t bt = blockIdx.x;
     uint32_t it = 0;
-    for (int k = 2; k < kPf; ++k) prefetch(bt + k * g);
     if (bt < nb) load(bt, va);
     if (bt + g < nb) load(bt + g, vb);
     while (bt < nb) {
-      prefetch(bt + kPf * g);
       if (!put(it, va)) break;
       ++it;
       bt += g;
       if (bt + g < nb) load(bt + g, va);
       if (bt >= nb) break;
-      prefetch(bt + kPf * g);
       if (!put(it, vb)) break;
       ++it;
       bt += g;
@@ -652,7 +642,14 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
     if (x3) return launch_tc<6, true, 3, true>(P, s);
     return launch_tc<6, false, 6, true>(P, s);
   }
-  if (P.contig && cb == 6) {  // tile rows are contiguous: bulk-staged loads
+  // Bulk-staged loads pay off only when a tile's rows lie in many different
+  // 2 MiB pages (five or more targets at qubit 18 or above: 32-64 pages per
+  // tile, beyond what the address translation caches hold), where they
+  // measured 7.3 ms against 9.6 ms per 30-qubit launch; elsewhere the
+  // register path is faster (3.1 against 4.0 ms).
+  int high = 0;
+  for (int j = 0; j < kTcK; ++j) high += a.targets[j] >= 18;
+  if (P.contig && cb == 6 && high >= 5) {
     if (x3) return launch_tc<6, true, 2, false, true, 2>(P, s);
     return launch_tc<6, false, 3, false, true, 3>(P, s);
   }
