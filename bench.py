@@ -392,7 +392,7 @@ def main():
                     help="override the plan's kernelization algorithm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--shm-max", type=int, default=13)
+    ap.add_argument("--shm-max", type=int, default=12)
     ap.add_argument("--workload", default="mixed", choices=["mixed", "entangling"])
     ap.add_argument("--profile-run", type=int, default=0, metavar="N",
                     help="plan the workload's circuit generator at N qubits and run the plan "
@@ -521,7 +521,8 @@ def main():
                    "n_qubits": n, "gates": int(len(gates)), "plan": label,
                    "kernels": int(ps.num_kernels), "shm_kernels": int(ps.num_shm),
                    "fused_kernels": int(ps.num_fused), "passes": int(ps.num_kernels),
-                   "planner_ms": ps.planner_ms, "jit_ms": ps.jit_ms, "l2": "no flush: the 8 GiB state exceeds L2",
+                   "planner_ms": ps.planner_ms, "jit_ms": ps.jit_ms, "shm_max_active": args.shm_max,
+                   "model_cost_ms": ps.cost / 1e3, "l2": "no flush: the 8 GiB state exceeds L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gates_per_s": len(gates) / (value * 1e-3),
         "hbm_roofline_frac_circuit": ps.num_kernels * pass_bytes / (value * 1e-3) / 1e9 / hbm,

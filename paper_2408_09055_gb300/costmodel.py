@@ -144,7 +144,7 @@ def _time_specs(n, specs, reps, st, s, threads, log=None):
 
 
 def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC_TF32X3, reps=3,
-           epochs=300, threads=None, log=print):
+           epochs=300, threads=None, log=print, weight=4, entangling_share=0.67):
     """Active refinement: plan freshly seeded workload circuits with the
     learned cost (Kernelize, fused kernels in `precision`), time exactly the
     kernels those plans chose, add them to the data and retrain.  A planner
@@ -161,12 +161,15 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
     fcost = Q.default_cost_table()
     for k in range(16):
         fcost.fuse_cost[k] = 1.0
-    metrics = {}
+    metrics, history = {}, []
+    Xr = np.zeros((0, X.shape[1]), dtype=np.float32)  # refinement samples (weighted)
+    yr = np.zeros(0, dtype=np.float32)
     for r in range(rounds):
         specs = []
         for c in range(circuits):
             wseed = 20_000 + int(rng.integers(0, 1 << 30))
-            g = C.mixed_circuit(n, 1200, wseed) if c % 2 else C.entangling_circuit(n, 10, wseed)
+            ent = rng.uniform() < entangling_share
+            g = C.entangling_circuit(n, 10, wseed) if ent else C.mixed_circuit(n, 1200, wseed)
             plan = Q.Plan(n, g, Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=precision, fuse_kmax=6,
                                                mlp=net, shm_variant=2))
             for k in range(plan.stats().num_kernels):
@@ -177,13 +180,22 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
                     opts = Q.default_opts(algo=Q.QS_ALGO_GREEDY, fuse_kmax=0, shm_max_active=14)
                 specs.append((sub, opts, opts.cost))
         Xn, yn, kinds = _time_specs(n, specs, reps, st, s, threads)
-        X = np.concatenate([X, np.asarray(Xn, dtype=np.float32)])
-        y = np.concatenate([y, np.asarray(yn, dtype=np.float32)])
-        net, metrics = train(X, y, epochs=epochs, seed=seed)
+        Xn = np.asarray(Xn, dtype=np.float32)
+        yn = np.asarray(yn, dtype=np.float32)
+        # bias of the current model on the kernels its own plans chose
+        pred = predict(net, Xn, stream=s)
+        bias = float(np.mean(np.exp(pred - yn)))
+        Xr, yr = np.concatenate([Xr, Xn]), np.concatenate([yr, yn])
+        Xt = np.concatenate([X] + [Xr] * weight)
+        yt = np.concatenate([y] + [yr] * weight)
+        net, metrics = train(Xt, yt, epochs=epochs, seed=seed)
+        history.append({"kernels": int(len(yn)), "fused": int(sum(kinds)), "pred_over_actual": bias})
         if log:
             log(f"refinement round {r + 1}: +{len(yn)} kernels ({sum(kinds)} fused), "
+                f"predicted/actual on them before retraining {bias:.3f}, "
                 f"test mean rel err {metrics['test']['mean_rel_err']:.3f}")
-    return net, X, y, metrics
+    metrics["refinement"] = history
+    return net, np.concatenate([X, Xr]), np.concatenate([y, yr]), metrics
 
 
 def split(count, seed=0, fractions=(0.8, 0.1, 0.1)):
@@ -272,9 +284,14 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--out", default=MODEL_PATH)
-    ap.add_argument("--refine-rounds", type=int, default=3)
+    ap.add_argument("--refine-rounds", type=int, default=6)
+    ap.add_argument("--data", default=None, help="reuse timed kernels saved by an earlier run")
     a = ap.parse_args(argv)
-    X, y, meta = generate(count=a.count, seed=a.seed)
+    if a.data:
+        d = np.load(a.data)
+        X, y, meta = d["X"], d["y"], json.loads(str(d["meta"]))
+    else:
+        X, y, meta = generate(count=a.count, seed=a.seed)
     net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print)
     if a.refine_rounds:
         net, X, y, metrics = refine(net, X, y, rounds=a.refine_rounds, seed=a.seed, epochs=a.epochs)
