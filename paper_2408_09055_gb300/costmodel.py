@@ -162,7 +162,8 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
     for k in range(16):
         fcost.fuse_cost[k] = 1.0
     metrics, history = {}, []
-    Xr = np.zeros((0, X.shape[1]), dtype=np.float32)  # refinement samples (weighted)
+    base = split(len(y), seed)
+    Xr = np.zeros((0, X.shape[1]), dtype=np.float32)  # refinement samples
     yr = np.zeros(0, dtype=np.float32)
     for r in range(rounds):
         specs = []
@@ -186,16 +187,22 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
         pred = predict(net, Xn, stream=s)
         bias = float(np.mean(np.exp(pred - yn)))
         Xr, yr = np.concatenate([Xr, Xn]), np.concatenate([yr, yn])
-        Xt = np.concatenate([X] + [Xr] * weight)
-        yt = np.concatenate([y] + [yr] * weight)
-        net, metrics = train(Xt, yt, epochs=epochs, seed=seed)
+        # held-out parts are split before the planner's choices are weighted
+        rtr, rva, rte = split(len(yr), seed + 1)
+        parts = [np.concatenate(p) for p in (
+            [X[base[0]]] + [Xr[rtr]] * weight, [y[base[0]]] + [yr[rtr]] * weight,
+            [X[base[1]], Xr[rva]], [y[base[1]], yr[rva]], [X[base[2]], Xr[rte]], [y[base[2]], yr[rte]])]
+        net, metrics = train_parts((parts[0], parts[1]), (parts[2], parts[3]), (parts[4], parts[5]),
+                                   epochs=epochs, seed=seed)
         history.append({"kernels": int(len(yn)), "fused": int(sum(kinds)), "pred_over_actual": bias})
         if log:
             log(f"refinement round {r + 1}: +{len(yn)} kernels ({sum(kinds)} fused), "
                 f"predicted/actual on them before retraining {bias:.3f}, "
                 f"test mean rel err {metrics['test']['mean_rel_err']:.3f}")
+    rtr, rva, rte = split(len(yr), seed + 1)
+    test_idx = np.concatenate([base[2], len(y) + rte]).astype(np.int64)
     metrics["refinement"] = history
-    return net, np.concatenate([X, Xr]), np.concatenate([y, yr]), metrics
+    return net, np.concatenate([X, Xr]), np.concatenate([y, yr]), metrics, test_idx
 
 
 def split(count, seed=0, fractions=(0.8, 0.1, 0.1)):
@@ -209,35 +216,44 @@ def train(X, y, hidden=128, epochs=200, batch=256, lr=1e-3, seed=0, stream=None,
     """Trains a fresh network on (X, y) with an 80/10/10 split; returns the
     network and a metrics dict (MSE of ln time; mean |relative error| of
     time) for the train, validation and test parts."""
-    import torch
     tr, va, te = split(len(y), seed)
+    return train_parts((X[tr], y[tr]), (X[va], y[va]), (X[te], y[te]), hidden, epochs, batch, lr, seed,
+                       stream, log)
+
+
+def train_parts(train_set, val_set, test_set, hidden=128, epochs=200, batch=256, lr=1e-3, seed=0,
+                stream=None, log=None):
+    """Trains on train_set, keeps the epoch with the best validation MSE,
+    reports metrics on all three (X, y) parts."""
+    import torch
+    Xtr, ytr = train_set
     dev = torch.device("cuda")
-    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
-    yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).to(dev)
+    Xd = torch.from_numpy(np.ascontiguousarray(Xtr, dtype=np.float32)).to(dev)
+    yd = torch.from_numpy(np.ascontiguousarray(ytr, dtype=np.float32)).to(dev)
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-    net = Q.Mlp(X.shape[1], hidden, seed)
+    net = Q.Mlp(Xtr.shape[1], hidden, seed)
     # centre the output on the mean target so training starts close
     theta = net.get_params()
-    theta[-1] = float(np.mean(y[tr]))
+    theta[-1] = float(np.mean(ytr))
     net.set_params(theta)
     rng = np.random.default_rng(seed + 1)
     best, best_theta = float("inf"), net.get_params()
     for ep in range(epochs):
-        order = tr[rng.permutation(len(tr))]
+        order = rng.permutation(len(ytr))
         for b0 in range(0, len(order), batch):
             idx = torch.from_numpy(order[b0:b0 + batch]).to(dev)
             xb = Xd.index_select(0, idx).contiguous()
             tb = yd.index_select(0, idx).contiguous()
             net.train_step(xb.data_ptr(), tb.data_ptr(), len(idx), lr, s)
         if ep % 10 == 9 or ep == epochs - 1:
-            v = evaluate(net, X[va], y[va], stream=s)["mse"]
+            v = evaluate(net, val_set[0], val_set[1], stream=s)["mse"]
             if v < best:
                 best, best_theta = v, net.get_params()
             if log:
                 log(f"epoch {ep + 1}: validation MSE {v:.4f}")
     net.set_params(best_theta)
-    metrics = {name: evaluate(net, X[ix], y[ix], stream=s) for name, ix in
-               (("train", tr), ("validation", va), ("test", te))}
+    metrics = {name: evaluate(net, part[0], part[1], stream=s) for name, part in
+               (("train", train_set), ("validation", val_set), ("test", test_set))}
     return net, metrics
 
 
@@ -293,11 +309,12 @@ def main(argv=None):
     else:
         X, y, meta = generate(count=a.count, seed=a.seed)
     net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print)
+    test_idx = split(len(y), a.seed)[2]
     if a.refine_rounds:
-        net, X, y, metrics = refine(net, X, y, rounds=a.refine_rounds, seed=a.seed, epochs=a.epochs)
+        net, X, y, metrics, test_idx = refine(net, X, y, rounds=a.refine_rounds, seed=a.seed, epochs=a.epochs)
         meta["refine_rounds"] = a.refine_rounds
         meta["count"] = int(len(y))
-    np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, meta=json.dumps(meta))
+    np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, test_idx=test_idx, meta=json.dumps(meta))
     meta["metrics"] = metrics
     save(net, a.out, meta)
     print(json.dumps(meta))
