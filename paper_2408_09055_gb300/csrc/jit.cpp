@@ -289,6 +289,24 @@ struct Gen {
           pc += 3;
           break;
         }
+        case PK_G2: {  // dense 4x4 on slots A < B
+          CF g[16];
+          for (int e = 0; e < 16; ++e) g[e] = cf(pc + 1 + 2 * e);
+          for (int j = 0; j < kRegAmps; ++j) {
+            if (((j >> A) & 1) || ((j >> B) & 1)) continue;
+            const int idx[4] = {j, j | (1 << A), j | (1 << B), j | (1 << A) | (1 << B)};
+            o << "{const float2 x0=" << v(idx[0]) << ",x1=" << v(idx[1]) << ",x2=" << v(idx[2])
+              << ",x3=" << v(idx[3]) << ";\n";
+            for (int i = 0; i < 4; ++i) {
+              std::vector<std::pair<CF, std::string>> t;
+              for (int k = 0; k < 4; ++k) t.push_back({g[4 * i + k], "x" + std::to_string(k)});
+              o << v(idx[i]) << "=make_float2(" << cre(t) << "," << cim(t) << ");\n";
+            }
+            o << "}\n";
+          }
+          pc += 33;
+          break;
+        }
         case PK_XCHG:
           ++xchg_seen;
           if (xchg_seen >= (int)pg.maps.size()) return false;

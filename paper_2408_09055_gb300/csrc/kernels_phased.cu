@@ -181,6 +181,28 @@ __device__ __forceinline__ void k_xx(Amps& a, float c, float s) {
   }
 }
 
+template <int S0, int S1>  // dense 4x4, index bit(S0) + 2 bit(S1), row-major in the program
+__device__ __forceinline__ void k_g2(Amps& a, const uint32_t* g) {
+#pragma unroll
+  for (int j = 0; j < kRegAmps; ++j) {
+    if (((j >> S0) & 1) || ((j >> S1) & 1)) continue;
+    const int idx[4] = {j, j | (1 << S0), j | (1 << S1), j | (1 << S0) | (1 << S1)};
+    const float2 x[4] = {a[idx[0]], a[idx[1]], a[idx[2]], a[idx[3]]};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float ur = __uint_as_float(__ldg(g + 2 * (4 * i + k)));
+        const float ui = __uint_as_float(__ldg(g + 2 * (4 * i + k) + 1));
+        re = fmaf(ur, x[k].x, fmaf(-ui, x[k].y, re));
+        im = fmaf(ur, x[k].y, fmaf(ui, x[k].x, im));
+      }
+      a[idx[i]] = make_float2(re, im);
+    }
+  }
+}
+
 __device__ __forceinline__ void k_scale(Amps& a, float2 e) {
 #pragma unroll
   for (int j = 0; j < kRegAmps; ++j) a[j] = cmul(a[j], e);
@@ -380,6 +402,10 @@ __global__ void __launch_bounds__(1 << (M - kRegBits), 1 << (kMaxShmActive - M))
         case PK_SCALE:
           k_scale(a, ldc(pc + 1));
           pc += 3;
+          break;
+        case PK_G2:
+          QS_PAIR(k_g2, A, B, a, pc + 1)
+          pc += 33;
           break;
         case PK_XCHG: {
           __syncthreads();  // every thread has finished reading the previous exchange

@@ -37,6 +37,7 @@ using cd = std::complex<double>;
 struct HostOp {
   uint32_t kind = PK_END, a = 0, b = REF_NONE, c = 0;
   cd m[4];                 // 2x2 matrix (row-major) or diagonal entries d[4]
+  cd g[16];                // PK_G2: 4x4, index bit(a) + 2 bit(b)
   double x0 = 0, x1 = 0;   // XX: cos, sin
   bool single_slot = false;  // uncontrolled one-slot matrix (mergeable)
   PhaseMap map;            // XCHG target map
@@ -104,6 +105,246 @@ uint32_t unit_mask(const cd* d) {
 }
 
 }  // namespace
+
+// ---- gate fusion inside a phase -------------------------------------------
+// Register ops on one or two slots commute with ops on other slots, so within
+// a phase the ops touching only slots {s} or {s, t} form blocks whose product
+// can replace them: a one-slot block becomes one 2x2, a two-slot block one
+// dense 4x4 (PK_G2) when that is cheaper than its ops one by one.
+
+// FP32 FMA-equivalents per amplitude of an op as the kernel applies it
+double op_cost(const HostOp& o) {
+  if (o.single_slot) {
+    const cd* M = o.m;
+    if (is_zero(M[1]) && is_zero(M[2])) return is_one(M[3] / M[0]) ? 0.0 : 2.0;
+    if (is_zero(M[0]) && is_zero(M[3])) return 0.5;
+    if ((is_real(M[0]) && is_real(M[1]) && is_real(M[2]) && is_real(M[3])) ||
+        (is_real(M[0]) && is_imag(M[1]) && is_imag(M[2]) && is_real(M[3])))
+      return 4.0;
+    return 8.0;
+  }
+  switch (o.kind) {
+    case PK_D2: return 4.0;
+    case PK_D2P: return 1.0;
+    case PK_XX: return 4.0;
+    case PK_G2: return 16.0;
+    default: return 0.0;  // renames (XGS, SWAPR)
+  }
+}
+
+bool fusable(const HostOp& o) {
+  if (o.single_slot) return true;
+  return o.kind == PK_D2 || o.kind == PK_D2P || o.kind == PK_XGS || o.kind == PK_SWAPR || o.kind == PK_XX;
+}
+
+// register slots an op reads or writes (known-bit references excluded)
+uint32_t slots_of(const HostOp& o) {
+  auto bit = [](uint32_t r) { return r < (uint32_t)kRegBits ? 1u << r : 0u; };
+  switch (o.single_slot ? PK_G1 : o.kind) {
+    case PK_G1: case PK_G1R: case PK_G1X: case PK_XG: case PK_XGK: case PK_D1: case PK_D1B: case PK_D1K:
+    case PK_G1C:
+      return bit(o.a) | (o.kind == PK_G1C ? bit(o.b) : 0u);
+    case PK_XGS: case PK_D2: case PK_D2P: case PK_SWAPR: case PK_XX: case PK_G2:
+      return bit(o.a) | bit(o.b);
+    default:
+      return 0u;  // D0, SCALE: scalar per thread
+  }
+}
+
+// the op as a 4x4 on slots (sa < sb), index bit(sa) + 2 bit(sb)
+void op_matrix4(const HostOp& o, uint32_t sa, uint32_t sb, cd* G) {
+  for (int e = 0; e < 16; ++e) G[e] = 0.0;
+  auto bits = [&](int i, uint32_t slot) { return slot == sa ? (i & 1) : (i >> 1); };
+  if (o.single_slot) {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        const int other_i = o.a == sa ? (i >> 1) : (i & 1), other_j = o.a == sa ? (j >> 1) : (j & 1);
+        if (other_i != other_j) continue;
+        G[4 * i + j] = o.m[2 * bits(i, o.a) + bits(j, o.a)];
+      }
+    return;
+  }
+  for (int j = 0; j < 4; ++j) {
+    const int ja = bits(j, o.a), jb = bits(j, o.b);  // column state on (o.a, o.b)
+    auto idx = [&](int xa, int xb) {  // index of the state with o.a = xa, o.b = xb
+      int i = 0;
+      i |= (o.a == sa ? xa : xb);
+      i |= (o.a == sa ? xb : xa) << 1;
+      return i;
+    };
+    switch (o.kind) {
+      case PK_D2:
+        G[4 * j + j] = o.m[ja + 2 * jb];
+        break;
+      case PK_D2P:
+        G[4 * j + j] = (ja && jb) ? o.m[3] : cd(1.0);
+        break;
+      case PK_XGS:  // target o.a, control o.b
+        G[4 * idx(jb ? 1 - ja : ja, jb) + j] = 1.0;
+        break;
+      case PK_SWAPR:
+        G[4 * idx(jb, ja) + j] = 1.0;
+        break;
+      case PK_XX:
+        G[4 * j + j] = o.x0;
+        G[4 * idx(1 - ja, 1 - jb) + j] = cd(0.0, -o.x1);
+        break;
+      case PK_G2:
+        for (int i = 0; i < 4; ++i) G[4 * i + j] = o.g[4 * i + j];  // same slot order by construction
+        break;
+      default:
+        break;
+    }
+  }
+}
+
+void matmul4(const cd* A, const cd* B, cd* C) {  // C = A B
+  cd t[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      cd acc = 0.0;
+      for (int k = 0; k < 4; ++k) acc += A[4 * i + k] * B[4 * k + j];
+      t[4 * i + j] = acc;
+    }
+  for (int e = 0; e < 16; ++e) C[e] = t[e];
+}
+
+// Appends one-slot matrix op `op` to ops, merged into the previous op when
+// that is a one-slot matrix on the same slot.
+void push_merged(std::vector<HostOp>& ops, const HostOp& op) {
+  if (op.single_slot && !ops.empty() && ops.back().single_slot && ops.back().a == op.a) {
+    HostOp& pr = ops.back();
+    const cd* A = pr.m;
+    const cd* B = op.m;
+    cd Cm[4] = {B[0] * A[0] + B[1] * A[2], B[0] * A[1] + B[1] * A[3],
+                B[2] * A[0] + B[3] * A[2], B[2] * A[1] + B[3] * A[3]};
+    for (int e = 0; e < 4; ++e) pr.m[e] = Cm[e];
+    return;
+  }
+  ops.push_back(op);
+}
+
+// Fuses the ops of one phase (no exchange inside) into `out`.
+void fuse_phase(const std::vector<HostOp>& in, std::vector<HostOp>& out) {
+  struct Block {
+    bool open = false;
+    uint32_t sa = 0, sb = 0;   // sb = sa: one-slot block
+    cd m2[4];                  // one-slot product
+    cd g[16];                  // two-slot product
+    std::vector<HostOp> orig;  // the ops, in order
+  };
+  std::vector<Block> blocks;
+  int of[kRegBits];
+  for (int i = 0; i < kRegBits; ++i) of[i] = -1;
+  auto close = [&](int bi) {
+    Block& b = blocks[bi];
+    if (!b.open) return;
+    b.open = false;
+    of[b.sa] = -1;
+    of[b.sb] = -1;
+    if (b.sa == b.sb) {  // one slot: the product, as one raw matrix
+      HostOp o;
+      o.kind = PK_G1;
+      o.single_slot = true;
+      o.a = b.sa;
+      for (int e = 0; e < 4; ++e) o.m[e] = b.m2[e];
+      push_merged(out, o);
+      return;
+    }
+    double c = 0;
+    for (const HostOp& o : b.orig) c += op_cost(o);
+    if (c > 16.0) {
+      HostOp o;
+      o.kind = PK_G2;
+      o.a = b.sa;
+      o.b = b.sb;
+      for (int e = 0; e < 16; ++e) o.g[e] = b.g[e];
+      out.push_back(o);
+    } else {
+      for (const HostOp& o : b.orig) push_merged(out, o);
+    }
+  };
+  auto embed_single = [&](const Block& s1, uint32_t sa, uint32_t sb, cd* G) {
+    HostOp t;
+    t.single_slot = true;
+    t.a = s1.sa;
+    for (int e = 0; e < 4; ++e) t.m[e] = s1.m2[e];
+    op_matrix4(t, sa, sb, G);
+  };
+  for (const HostOp& op : in) {
+    const uint32_t sl = slots_of(op);
+    if (!fusable(op)) {
+      for (int s = 0; s < kRegBits; ++s)
+        if (((sl >> s) & 1) && of[s] >= 0) close(of[s]);
+      out.push_back(op);
+      continue;
+    }
+    if (op.single_slot) {
+      const uint32_t s = op.a;
+      if (of[s] < 0) {
+        Block b;
+        b.open = true;
+        b.sa = b.sb = s;
+        for (int e = 0; e < 4; ++e) b.m2[e] = op.m[e];
+        b.orig.push_back(op);
+        of[s] = (int)blocks.size();
+        blocks.push_back(std::move(b));
+        continue;
+      }
+      Block& b = blocks[of[s]];
+      b.orig.push_back(op);
+      if (b.sa == b.sb) {
+        const cd* A = b.m2;
+        const cd* B = op.m;
+        cd Cm[4] = {B[0] * A[0] + B[1] * A[2], B[0] * A[1] + B[1] * A[3],
+                    B[2] * A[0] + B[3] * A[2], B[2] * A[1] + B[3] * A[3]};
+        for (int e = 0; e < 4; ++e) b.m2[e] = Cm[e];
+      } else {
+        cd G[16];
+        op_matrix4(op, b.sa, b.sb, G);
+        matmul4(G, b.g, b.g);
+      }
+      continue;
+    }
+    // a two-slot op
+    const uint32_t sa = std::min(op.a, op.b), sb = std::max(op.a, op.b);
+    int ba = of[sa], bb = of[sb];
+    if (ba >= 0 && ba == bb && blocks[ba].sa != blocks[ba].sb) {
+      Block& b = blocks[ba];
+      b.orig.push_back(op);
+      cd G[16];
+      op_matrix4(op, sa, sb, G);
+      matmul4(G, b.g, b.g);
+      continue;
+    }
+    // blocks pairing sa or sb with a third slot end here
+    for (int x : {ba, bb})
+      if (x >= 0 && blocks[x].open && blocks[x].sa != blocks[x].sb) close(x);
+    ba = of[sa];
+    bb = of[sb];
+    Block nb;
+    nb.open = true;
+    nb.sa = sa;
+    nb.sb = sb;
+    for (int e = 0; e < 16; ++e) nb.g[e] = (e % 5 == 0) ? cd(1.0) : cd(0.0);
+    for (int x : {ba, bb}) {  // absorb the one-slot blocks (they commute)
+      if (x < 0) continue;
+      Block& s1 = blocks[x];
+      cd G[16];
+      embed_single(s1, sa, sb, G);
+      matmul4(G, nb.g, nb.g);
+      for (const HostOp& o : s1.orig) nb.orig.push_back(o);
+      s1.open = false;
+    }
+    nb.orig.push_back(op);
+    cd G[16];
+    op_matrix4(op, sa, sb, G);
+    matmul4(G, nb.g, nb.g);
+    of[sa] = of[sb] = (int)blocks.size();
+    blocks.push_back(std::move(nb));
+  }
+  for (size_t bi = 0; bi < blocks.size(); ++bi) close((int)bi);
+}
 
 bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, ShmProgramV2* out) {
   const int m = sp.m;
@@ -194,18 +435,17 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
   };
   auto is_slot = [](uint32_t rf) { return rf < (uint32_t)kRegBits; };
 
-  auto push = [&](HostOp op) {
-    // merge consecutive uncontrolled one-slot matrices on the same slot
-    if (op.single_slot && !ops.empty() && ops.back().single_slot && ops.back().a == op.a) {
-      HostOp& pr = ops.back();
-      const cd* A = pr.m;
-      const cd* B = op.m;
-      cd Cm[4] = {B[0] * A[0] + B[1] * A[2], B[0] * A[1] + B[1] * A[3],
-                  B[2] * A[0] + B[3] * A[2], B[2] * A[1] + B[3] * A[3]};
-      for (int e = 0; e < 4; ++e) pr.m[e] = Cm[e];
-      return;
+  // ops of the current phase, fused when the phase ends
+  std::vector<HostOp> phase_ops;
+  const bool fuse = p->opts.shm_variant != 2;  // the interpreter keeps the plain ops
+  auto push = [&](HostOp op) { phase_ops.push_back(op); };
+  auto end_phase = [&]() {
+    if (fuse) {
+      fuse_phase(phase_ops, ops);
+    } else {
+      for (const HostOp& o : phase_ops) push_merged(ops, o);
     }
-    ops.push_back(op);
+    phase_ops.clear();
   };
 
   auto emit = [&](const Gate& g) -> bool {
@@ -312,6 +552,7 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
     nr = fill_regs(nr, tmask, done, m, 0);
     cur = make_map(nr, m);
     set_slots(cur);
+    end_phase();
     HostOp x;
     x.kind = PK_XCHG;
     x.map = cur;
@@ -319,6 +560,7 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
     out->maps.push_back(cur);
     ++phases;
   }
+  end_phase();
   // store phase: register bits must avoid the low local bits
   uint32_t rmask = 0;
   for (int i = 0; i < kRegBits; ++i) rmask |= 1u << cur.R[i];
@@ -394,6 +636,12 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
       case PK_XX:
         fl(o.x0);
         fl(o.x1);
+        break;
+      case PK_G2:
+        for (int e = 0; e < 16; ++e) {
+          fl(o.g[e].real());
+          fl(o.g[e].imag());
+        }
         break;
       case PK_XCHG:
         w.back() = PK_XCHG | ((uint32_t)o.map.nt << 8);

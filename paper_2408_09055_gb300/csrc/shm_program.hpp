@@ -34,6 +34,7 @@ enum : uint32_t {
   PK_XX = 15,     // a = slot0 < b = slot1; 2 floats (cos t/2, sin t/2)
   PK_SCALE = 16,  // 2 floats: every amplitude times a constant
   PK_XCHG = 17,   // a = thread bits nt; 5 words er[], nt words (tloc | tswz << 16)
+  PK_G2 = 18,     // a = slot0 < b = slot1; 32 floats: general 4x4, index bit(a) + 2 bit(b), row-major
 };
 
 // qubit references inside an op
