@@ -4,8 +4,10 @@ The committed network (trained on kernels timed on GB300, BF16 inference in
 the library's kernels) and the analytic cost ("Cost Function in Kernelize":
 alpha + the sum of per-gate costs for a shared-memory kernel, a constant
 per width for a fused kernel) both predict the run time of the same
-held-out timed kernels.  The analytic form is given its best chance: its
-constants are least-squares fitted on the other timed kernels."""
+held-out timed kernels: once with the library's built-in analytic table
+(the cost the analytic plans use) and once with the analytic form given its
+best chance, its constants least-squares fitted on the other timed
+kernels."""
 import os
 
 import numpy as np
@@ -34,9 +36,14 @@ def test_learned_cost_beats_the_analytic_cost_on_held_out_kernels():
     learned = np.exp(CM.predict(net, X[test]).astype(np.float64))
     M = _analytic_design(X)
     coef, *_ = np.linalg.lstsq(M[rest], t[rest], rcond=None)
-    analytic = M[test] @ coef
-    e_learned = float(np.mean(np.abs(learned / t[test] - 1)))
-    e_analytic = float(np.mean(np.abs(analytic / t[test] - 1)))
+    fitted = M[test] @ coef
+    from paper_2408_09055_gb300 import qsim as Q
+    tab = Q.default_cost_table()
+    per_type = np.array([tab.gate_cost[k] for k in range(10)])
+    table = np.where(X[test, 41] > 0.5, tab.fuse_cost[6], tab.alpha + np.rint(X[test, 30:40] * 16.0) @ per_type)
+    err = lambda p: float(np.mean(np.abs(p / t[test] - 1)))
+    e_learned, e_fitted, e_table = err(learned), err(fitted), err(table)
     assert len(test) > 500
     assert e_learned < 0.12, e_learned
-    assert e_learned < 0.75 * e_analytic, (e_learned, e_analytic)
+    assert e_learned < 0.9 * e_fitted, (e_learned, e_fitted)
+    assert e_learned < 0.5 * e_table, (e_learned, e_table)
