@@ -391,6 +391,8 @@ def main():
     ap.add_argument("--algo", default=None, choices=[None, "ordered", "kernelize"],
                     help="override the plan's kernelization algorithm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="with --plan A, skip timing plan B beside it")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--shm-max", type=int, default=12)
     ap.add_argument("--workload", default="mixed", choices=["mixed", "entangling"])
@@ -536,6 +538,41 @@ def main():
                 "norm2_out": e2e_norm},
     }
     del host_in, host_out
+    if args.plan == "A" and not args.no_compare:
+        # the learned-cost plan with fused 3xTF32 kernels, timed the same way
+        # on the same state (the metric's second arm)
+        plan_b, label_b = make_plan(Q, gates, "B", args.shm_max, args.algo)
+        bs = plan_b.stats()
+        for _ in range(args.warmup):
+            st.run(plan_b, sp)
+        torch.cuda.synchronize()
+        tb = Q.Timer(plan_b, args.steps)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            st.run_timed(plan_b, tb, sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([b_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            b_ms = float(t.item())
+        pk, rb = tb.read()
+        kd = [plan_b.kernel(k) for k in range(bs.num_kernels)]
+        shm_ms = [pk[k] / rb for k in range(bs.num_kernels) if kd[k].type == Q.QS_KERNEL_SHM]
+        line["plan_b"] = {
+            "plan": label_b, "value": b_ms / (args.steps * world), "unit": "ms/circuit",
+            "dtype": "f32 shared-memory kernels, tf32x3 fused kernels",
+            "kernels": int(bs.num_kernels), "fused_kernels": int(bs.num_fused),
+            "model_cost_ms": bs.cost / 1e3, "planner_ms": bs.planner_ms,
+            "shm_avg_launch_ms": float(np.mean(shm_ms)) if shm_ms else None,
+            "shm_roofline_frac": (pass_bytes / (float(np.mean(shm_ms)) * 1e-3) / 1e9 / hbm) if shm_ms else None,
+            "norm2_after": st.norm2(sp),
+            "speedup_over_plan_a": (elapsed_ms / args.steps) / (b_ms / args.steps),
+        }
     if plan.opts.precision != Q.QS_PREC_FP32:
         line["dtype"] = {Q.QS_PREC_TF32: "tf32", Q.QS_PREC_TF32X3: "tf32x3"}[plan.opts.precision]
     if rank == 0 and not args.no_cpu_baseline:
