@@ -480,8 +480,15 @@ def main():
     avg_ms = by_type[dom][0] / max(by_type[dom][1], 1)
     hbm, _, src = peaks()
     achieved = pass_bytes / (avg_ms * 1e-3) / 1e9
+    # DRAM bytes per launch: the ncu capture of the specialised kernel at 28
+    # qubits (profiles/qsk_shm_kernel_n28_full.md) moved 0.986 of the
+    # algorithmic bytes; scaled to this state (traffic grows with 2^n)
+    traffic = 0.986 * pass_bytes if dom.startswith("qsk") else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "frac": achieved / hbm, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read+write of the same kernel at 28 qubits, scaled x4"
+                               if traffic else None),
+            "peak_source": src,
             "launches_timed": by_type[dom][1], "avg_launch_ms": avg_ms,
             "share_of_step": by_type[dom][0] / max(sum(v[0] for v in by_type.values()), 1e-12)}
 
