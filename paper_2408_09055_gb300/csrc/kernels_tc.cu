@@ -2,21 +2,23 @@
 // TF32 and split-precision 3xTF32 (Sec. 6.2 "Fusion" kernels: the product of
 // a kernel's gates applied as one dense unitary).
 //
-// The complex 2^6 x 2^6 unitary U = Ur + i Ui becomes the real 128 x 128 block
-// matrix W = [[Ur, -Ui], [Ui, Ur]] (the A operand).  A tile of the state --
-// 64 target rows by N columns (the lowest non-target qubits) -- becomes the
-// real 128 x N matrix [Re X; Im X] (the B operand), and D = W B lands in
-// tensor memory as fp32.  For 3xTF32, W = Wh + Wl is split on the host and
-// B = Bh + Bl on the device (Bh = B rounded to TF32, Bl = B - Bh), and
-// D = Wh Bh + Wh Bl + Wl Bh recovers close to FP32 accuracy (Markidis et al.
-// 2018; Ootomo and Yokota 2022).
+// The complex 2^6 x 2^6 unitary U = Ur + i Ui becomes a real 128 x 128 matrix
+// W (the A operand, held in tensor memory for the whole launch): its rows and
+// columns interleave real and imaginary parts, so W (Re x0, Im x0, Re x1, ...)
+// = (Re y0, Im y0, ...) for y = U x.  A tile of the state -- 64 target rows by
+// N columns (the lowest non-target qubits) -- is the real 128 x N B operand
+// in shared memory, and D = W B lands in tensor memory as fp32.  For 3xTF32,
+// W = Wh + Wl is split on the host and B = Bh + Bl on the device (Bh = B
+// rounded to TF32, Bl = B - Bh), and D = Wh Bh + Wh Bl + Wl Bh recovers close
+// to FP32 accuracy (Markidis et al. 2018; Ootomo and Yokota 2022).
 //
-// Shared-memory operands use the K-major, no-swizzle canonical layout: core
-// matrices of 8 rows x 16 bytes (4 TF32), adjacent along K 128 B apart
-// (leading byte offset) and along M/N (K/4)*128 B apart (stride byte offset).
-// One thread issues the MMAs; completion is signalled by tcgen05.commit on an
-// mbarrier whose wait is bounded in time (an expired wait sets an error flag,
-// the CTA frees its tensor memory and returns).
+// The B operand uses the K-major, no-swizzle canonical layout: core matrices
+// of 8 rows x 16 bytes (4 TF32), adjacent along K 128 B apart (leading byte
+// offset) and along N (K/4)*128 B apart (stride byte offset).  One thread
+// issues the MMAs; completion is signalled by tcgen05.commit on mbarriers
+// whose waits are bounded in time (an expired wait sets an error flag, every
+// role leaves its loop, in-flight operations are waited for, tensor memory
+// is freed and the CTA returns).
 #include <algorithm>
 #include <cstring>
 #include <mutex>

@@ -437,14 +437,9 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
 
   // ops of the current phase, fused when the phase ends
   std::vector<HostOp> phase_ops;
-  const bool fuse = p->opts.shm_variant != 2;  // the interpreter keeps the plain ops
   auto push = [&](HostOp op) { phase_ops.push_back(op); };
   auto end_phase = [&]() {
-    if (fuse) {
-      fuse_phase(phase_ops, ops);
-    } else {
-      for (const HostOp& o : phase_ops) push_merged(ops, o);
-    }
+    fuse_phase(phase_ops, ops);
     phase_ops.clear();
   };
 
