@@ -107,6 +107,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    replica's); x itself when there is one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -454,11 +466,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    elapsed_ms = e0.elapsed_time(e1)
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         dist.barrier()
     per_kernel_ms, runs = timer.read()
     norm = st.norm2(sp)
@@ -511,11 +520,7 @@ def main():
         st.run(plan, sp)
         st.read(out=hout, stream=sp)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, "cuda")
     e2e_norm = float(np.sum(np.abs(hout.astype(np.complex128)) ** 2))
 
     value = elapsed_ms / (args.steps * world)
@@ -562,11 +567,7 @@ def main():
             st.run_timed(plan_b, tb, sp)
         e1.record(stream)
         torch.cuda.synchronize()
-        b_ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([b_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            b_ms = float(t.item())
+        b_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         pk, rb = tb.read()
         kd = [plan_b.kernel(k) for k in range(bs.num_kernels)]
         shm_ms = [pk[k] / rb for k in range(bs.num_kernels) if kd[k].type == Q.QS_KERNEL_SHM]
