@@ -197,6 +197,9 @@ typedef struct qs_state qs_state;
  * aligned) is used and stays owned by the caller.  Contents are undefined
  * until qs_state_set_zero or qs_write_amplitudes.                          */
 int qs_state_create(int32_t n, void* device_ptr, qs_state** out);
+/* A library-owned state of n qubits (1..34) initialised to |0...0>,
+ * stream-ordered on `stream` (qs_state_create + qs_state_set_zero).        */
+int qs_alloc_state(int32_t n, void* stream, qs_state** out);
 void qs_state_free(qs_state* st);
 void* qs_state_device_ptr(const qs_state* st);
 int qs_state_set_zero(qs_state* st, void* stream); /* |0...0> */

@@ -490,6 +490,17 @@ int qs_state_create(int32_t n, void* device_ptr, qs_state** out) {
   return QS_OK;
 }
 
+int qs_alloc_state(int32_t n, void* stream, qs_state** out) {
+  int rc = qs_state_create(n, nullptr, out);
+  if (rc != QS_OK) return rc;
+  rc = qs_state_set_zero(*out, stream);
+  if (rc != QS_OK) {
+    qs_state_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
 void qs_state_free(qs_state* s) {
   if (!s) return;
   if (s->owned && s->psi) cudaFree(s->psi);

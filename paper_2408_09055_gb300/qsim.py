@@ -95,6 +95,7 @@ def _load():
         "qs_plan_validate": ([vp, vp, u64], ctypes.c_int),
         "qs_plan_kernel_source": ([vp, u64, ctypes.c_char_p, u64], i64),
         "qs_state_create": ([i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "qs_alloc_state": ([i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "qs_state_free": ([vp], None),
         "qs_state_device_ptr": ([vp], vp),
         "qs_state_set_zero": ([vp, vp], ctypes.c_int),
@@ -316,6 +317,16 @@ class HostTimer:
 class State:
     """Owns a ``qs_state*``; ``device_ptr`` (e.g. a torch tensor's data_ptr)
     makes it a view of caller memory."""
+
+    @classmethod
+    def alloc(cls, n: int, stream=None) -> "State":
+        """qs_alloc_state: a library-owned state initialised to |0...0>."""
+        self = cls.__new__(cls)
+        h = ctypes.c_void_p()
+        check(_lib.qs_alloc_state(int(n), _stream_ptr(stream), ctypes.byref(h)), "qs_alloc_state")
+        self.h = h
+        self.n = n
+        return self
 
     def __init__(self, n: int, device_ptr: int | None = None):
         h = ctypes.c_void_p()

@@ -167,3 +167,16 @@ def test_host_timer_timeline_is_ordered():
     assert T.shape == (plan.stats().num_stages, 1 << (n - L), 4)
     assert np.all(T >= 0) and np.all(np.diff(T, axis=2) >= 0)
     assert_close_state(v.copy(), sim.apply(n, g))
+
+
+def test_alloc_state_starts_at_zero_and_runs_a_plan():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 15
+    g = C.mixed_circuit(n, 200, 51)
+    s = torch.cuda.current_stream().cuda_stream
+    st = Q.State.alloc(n, s)
+    v = st.read(stream=s)
+    assert v[0] == 1 and np.count_nonzero(v) == 1
+    st.run(Q.Plan(n, g), s)
+    assert_close_state(st.read(stream=s), sim.apply(n, g))

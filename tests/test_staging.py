@@ -104,3 +104,17 @@ def test_staged_plan_has_no_resident_form():
     assert e.value.status == -3
     with pytest.raises(Q.QsError):
         Q.Timer(p, 1)
+
+
+def test_host_run_rejects_bad_arguments_before_device_work():
+    # a misaligned or missing host state is refused before any CUDA call
+    import ctypes
+    n = 14
+    p = Q.Plan(n, C.mixed_circuit(n, 40, 3), local_qubits=12, shm_max_active=12, shm_variant=2)
+    with pytest.raises(Q.QsError) as e:
+        p.run_host(0)
+    assert e.value.status == -1
+    with pytest.raises(Q.QsError) as e:
+        p.run_host(1 << 20 | 8)  # not 16-byte aligned
+    assert e.value.status == -1
+    assert Q._lib.qs_run_plan_host(None, None, None, 0, None) == -1
