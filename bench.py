@@ -307,6 +307,39 @@ def _copy_peaks(torch, host, dev, nbytes, reps=3):
     return out
 
 
+def remap_measure(args):
+    """qs_remap (Alg. 1's Shard permutation) on an n-qubit resident state:
+    one HBM pass per call (every amplitude read and written once); CUDA
+    events over `steps` calls after `warmup`, for several bit permutations."""
+    import numpy as np
+    import torch
+    from paper_2408_09055_gb300 import qsim as Q
+    n = args.remap
+    src = torch.zeros(2 << n, dtype=torch.float32, device="cuda")
+    dst = torch.empty_like(src)
+    s = torch.cuda.current_stream()
+    rng = np.random.default_rng(0)
+    perms = {"identity": np.arange(n), "reverse": np.arange(n)[::-1], "random": rng.permutation(n),
+             "low 5 <-> high 5": np.r_[np.arange(n - 5, n), np.arange(5, n - 5), np.arange(0, 5)]}
+    hbm, _, src_kind = peaks()
+    out = {}
+    for name, perm in perms.items():
+        for _ in range(args.warmup):
+            Q.qs_remap(src.data_ptr(), dst.data_ptr(), n, perm, s.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            Q.qs_remap(src.data_ptr(), dst.data_ptr(), n, perm, s.cuda_stream)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        gbs = 16.0 * (1 << n) / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "GB/s": gbs, "frac": gbs / hbm}
+    print(json.dumps({"metric": "qubit remap (bit permutation) bandwidth", "n_qubits": n,
+                      "peak_gbs": hbm, "peak_source": src_kind, "steps": args.steps, "permutations": out}))
+    return 0
+
+
 def staged_measure(args):
     """Staged execution (Alg. 1's Execute over host memory): a layered
     U3 + CZ circuit (30 layers, seed 0) on an n-qubit state in page-locked
@@ -416,8 +449,12 @@ def main():
                     help="measure staged execution instead: an N-qubit state in page-locked host "
                          "memory, run chunk by chunk with --local-qubits L")
     ap.add_argument("--local-qubits", type=int, default=0)
+    ap.add_argument("--remap", type=int, default=0, metavar="N",
+                    help="measure the qubit-remap kernel on an N-qubit state instead")
     ap.add_argument("--chunk-buffers", type=int, default=4, choices=[1, 2, 3, 4])
     args = ap.parse_args()
+    if args.remap:
+        return remap_measure(args)
     if args.staged:
         return staged_measure(args)
     if args.profile_run:

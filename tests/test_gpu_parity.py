@@ -138,12 +138,14 @@ def test_norm_and_compare_reductions():
     assert abs(mx - np.max(np.abs(ref - got))) < 1e-7
 
 
-@pytest.mark.parametrize("n", [6, 14, 21])
-def test_remap_permutes_bits(n):
+@pytest.mark.parametrize("kind", ["random", "identity", "reverse", "rotate"])
+@pytest.mark.parametrize("n", [6, 10, 14, 21])
+def test_remap_permutes_bits(n, kind):
     need_gpu()
     from paper_2408_09055_gb300 import qsim as Q
     rng = np.random.default_rng(n)
-    perm = rng.permutation(n)
+    perm = {"random": rng.permutation(n), "identity": np.arange(n), "reverse": np.arange(n)[::-1],
+            "rotate": (np.arange(n) + 7) % n}[kind]
     x = (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)).astype(np.complex64)
     src = torch.from_numpy(x.view(np.float32)).cuda()
     dst = torch.empty_like(src)
