@@ -185,3 +185,38 @@ def test_bad_gate_rejected():
         sim.apply(3, C.make_gates([(C.CX, 1, 1)]))
     with pytest.raises(ValueError):
         sim.apply(3, C.make_gates([(C.H, 5)]))
+
+
+def _golden_pairs():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "eq1_pair_indices.txt")
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        head, body = line.split(":")
+        n, q = (int(x) for x in head.split())
+        pairs = [tuple(int(x) for x in p.split()) for p in body.split(";")]
+        yield n, q, pairs
+
+
+def test_one_qubit_gate_follows_eq1_pair_indices():
+    # the oracle updates exactly the pairs Eq. 1 names, with u00 acting on
+    # the lower index of each pair (fixture: tests/golden/eq1_pair_indices.txt)
+    import numpy as np
+    from oracle import sim
+    from synth import circuits as C
+    cases = list(_golden_pairs())
+    assert len(cases) == 5
+    for n, q, pairs in cases:
+        assert len(pairs) == 2 ** (n - 1)
+        rng = np.random.default_rng(10 * n + q)
+        psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+        g = C.make_gates([(C.U3, q, None, 0.7, 1.1, -0.4)])
+        u = sim.gate_matrix(C.U3, (0.7, 1.1, -0.4))
+        out = sim.apply(n, g, psi.copy())
+        expect = psi.copy()
+        for a, b in pairs:
+            expect[a] = u[0, 0] * psi[a] + u[0, 1] * psi[b]
+            expect[b] = u[1, 0] * psi[a] + u[1, 1] * psi[b]
+        assert np.allclose(out, expect, atol=1e-14)
