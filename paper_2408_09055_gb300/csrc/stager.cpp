@@ -3,14 +3,15 @@
 // non-insular qubit of the stage's gates (insular qubits may be regional:
 // their value is fixed within a chunk, Definition 2).
 //
-// The stager is greedy over stages, in the spirit of the SnuQS baseline the
-// paper compares against (Sec. 6): each stage takes as many gates as it can.
-// With the frontier fixed, the regional qubits of the next stage are chosen
-// among the freely placeable ones (all but the L - kStageSlots lowest) by
-// trying every choice when there are at most kMaxChoices of them and keeping
-// the one that admits the most gates; otherwise the local set grows in
-// circuit order until the next gate no longer fits and the free slots go to
-// the qubits the remaining gates need first.  Gates on disjoint qubits
+// The stager searches over sequences of local sets in the spirit of the
+// SnuQS baseline the paper compares against (Sec. 6), which takes as many
+// gates per stage as it can: the regional qubits of a stage are chosen among
+// the freely placeable ones (all but the L - kStageSlots lowest) by trying
+// every choice when there are at most kMaxChoices of them (otherwise the
+// local set grows in circuit order until the next gate no longer fits and
+// the free slots go to the qubits the remaining gates need first), and a beam
+// search keeps several of the best partial stagings so that a stage that
+// takes slightly fewer gates can still lead to fewer stages overall.  Gates on disjoint qubits
 // commute, so a stage takes every gate whose non-insular qubits are local
 // and that shares no qubit with an earlier gate left for a later stage.
 #include <bit>
@@ -82,6 +83,86 @@ uint64_t grow_in_order(const std::vector<Gate>& g, const std::vector<int32_t>& r
 
 }  // namespace
 
+// Local sets of a stage: every choice of the regional qubits among the free
+// ones (when there are at most kMaxChoices), ranked by the gates they admit;
+// else the first-come set alone.
+std::vector<std::pair<size_t, uint64_t>> stage_choices(const std::vector<Gate>& g,
+                                                       const std::vector<int32_t>& rest, int n, int L,
+                                                       int jlow, uint64_t low, uint64_t all) {
+  std::vector<std::pair<size_t, uint64_t>> out;
+  const int free_q = n - jlow, nreg = n - L;
+  if (binom(free_q, nreg) > kMaxChoices) {
+    const uint64_t S = grow_in_order(g, rest, low, all, n, L);
+    out.push_back({admitted(g, rest, S, all, nullptr, nullptr), S});
+    return out;
+  }
+  std::vector<int> pick(nreg);
+  std::iota(pick.begin(), pick.end(), jlow);
+  while (true) {
+    uint64_t R = 0;
+    for (int q : pick) R |= 1ull << q;
+    const uint64_t S = all & ~R;
+    out.push_back({admitted(g, rest, S, all, nullptr, nullptr), S});
+    int t = nreg - 1;  // next combination in lexicographic order
+    while (t >= 0 && pick[t] == n - nreg + t) --t;
+    if (t < 0) break;
+    pick[t]++;
+    for (int u = t + 1; u < nreg; ++u) pick[u] = pick[u - 1] + 1;
+  }
+  // most gates first; ties keep the lexicographic order of the regional set
+  std::stable_sort(out.begin(), out.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  return out;
+}
+
+// Beam search over stage sequences: every partial staging keeps its
+// remaining gates; each step expands the kBeam partial stagings that covered
+// the most gates by their kExpand best local sets.  All partial stagings of
+// a step have the same number of stages, so the first to cover every gate
+// uses the fewest stages the search saw (greedy, one set per stage, is the
+// width-1 case).
+constexpr int kBeam = 6, kExpand = 6;
+
+std::vector<uint64_t> choose_local_sets(const std::vector<Gate>& g, const std::vector<int32_t>& rest0, int n,
+                                        int L, int jlow, uint64_t low, uint64_t all) {
+  struct Partial {
+    std::vector<int32_t> rest;
+    std::vector<uint64_t> sets;
+  };
+  std::vector<Partial> beam(1);
+  beam[0].rest = rest0;
+  while (true) {
+    std::vector<Partial> next;
+    for (const Partial& p : beam) {
+      const auto ch = stage_choices(g, p.rest, n, L, jlow, low, all);
+      for (size_t k = 0; k < ch.size() && k < (size_t)kExpand; ++k) {
+        if (ch[k].first == 0) break;
+        Partial c;
+        c.sets = p.sets;
+        c.sets.push_back(ch[k].second);
+        admitted(g, p.rest, ch[k].second, all, nullptr, &c.rest);
+        if (c.rest.empty()) return c.sets;
+        next.push_back(std::move(c));
+      }
+    }
+    if (next.empty()) return {};
+    std::stable_sort(next.begin(), next.end(),
+                     [](const Partial& a, const Partial& b) { return a.rest.size() < b.rest.size(); });
+    // distinct remaining sets only (different choices often leave the same gates)
+    std::vector<Partial> keep;
+    for (Partial& c : next) {
+      bool dup = false;
+      for (const Partial& k : keep)
+        if (k.rest == c.rest) {
+          dup = true;
+          break;
+        }
+      if (!dup) keep.push_back(std::move(c));
+      if ((int)keep.size() == kBeam) break;
+    }
+    beam.swap(keep);
+  }
+}
+
 int stage_circuit(const std::vector<Gate>& g, int n, int L, std::vector<Stage>* out) {
   out->clear();
   if (L < 2 || L > n) return QS_EINVAL;
@@ -92,32 +173,12 @@ int stage_circuit(const std::vector<Gate>& g, int n, int L, std::vector<Stage>* 
   std::iota(rest.begin(), rest.end(), 0);
   for (const Gate& x : g)
     if (std::popcount(low | x.nimask) > L) return QS_EPLAN;
+  // the local sets of all stages, by a beam search over the greedy choices
+  const std::vector<uint64_t> plan = choose_local_sets(g, rest, n, L, jlow, low, all);
+  size_t next = 0;
   while (!rest.empty()) {
-    uint64_t S = 0;
-    const int free_q = n - jlow, nreg = n - L;
-    if (binom(free_q, nreg) <= kMaxChoices) {
-      // every choice of the regional qubits among the free ones
-      std::vector<int> pick(nreg);
-      std::iota(pick.begin(), pick.end(), jlow);
-      size_t best = 0;
-      S = all;
-      while (true) {
-        uint64_t R = 0;
-        for (int q : pick) R |= 1ull << q;
-        const size_t c = admitted(g, rest, all & ~R, all, nullptr, nullptr);
-        if (c > best || S == all) {
-          best = c;
-          S = all & ~R;
-        }
-        int t = nreg - 1;  // next combination in lexicographic order
-        while (t >= 0 && pick[t] == n - nreg + t) --t;
-        if (t < 0) break;
-        pick[t]++;
-        for (int u = t + 1; u < nreg; ++u) pick[u] = pick[u - 1] + 1;
-      }
-    } else {
-      S = grow_in_order(g, rest, low, all, n, L);
-    }
+    if (next >= plan.size()) return QS_EPLAN;
+    const uint64_t S = plan[next++];
     // the stage: every gate the final set admits, in circuit order
     Stage st;
     st.local = S;
