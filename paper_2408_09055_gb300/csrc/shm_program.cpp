@@ -153,6 +153,7 @@ uint32_t slots_of(const HostOp& o) {
 
 // the op as a 4x4 on slots (sa < sb), index bit(sa) + 2 bit(sb)
 void op_matrix4(const HostOp& o, uint32_t sa, uint32_t sb, cd* G) {
+  (void)sb;  // index bit 1 is slot sb: every slot of the op that is not sa
   for (int e = 0; e < 16; ++e) G[e] = 0.0;
   auto bits = [&](int i, uint32_t slot) { return slot == sa ? (i & 1) : (i >> 1); };
   if (o.single_slot) {
