@@ -173,6 +173,18 @@ int qs_plan_fused_matrix(const qs_plan* plan, uint64_t k, double* out, uint64_t 
  * length (excluding the NUL), or a negative status (QS_EINVAL when kernel k
  * has no specialised form).  With out == NULL only the length is returned. */
 int64_t qs_plan_kernel_source(const qs_plan* plan, uint64_t k, char* out, uint64_t cap);
+/* The register-phased program of shared-memory kernel k -- the words the
+ * interpreter runs and the specialised kernel is generated from (opcodes and
+ * operand layout in shm_program.hpp) -- for inspection and testing.  Copies
+ * up to `cap` words into `words` (NULL: only the count is returned) and, when
+ * `layout` is non-NULL, 20 integers into it: m, the physical qubits of the
+ * m active local bits (14 entries, -1 past m), and the local bits of the 5
+ * register slots in the first phase.  Staged plans report positions in the
+ * stage's chunk view.  Returns the word count, or QS_EINVAL when kernel k has
+ * no register-phased program (fused kernels, tiles below 2^10).            */
+int64_t qs_plan_kernel_program(const qs_plan* plan, uint64_t k, uint32_t* words, uint64_t cap,
+                               int32_t* layout);
+
 /* Checks Theorem 2 on a plan: every gate exactly once and, for every pair of
  * gates sharing a qubit that is not insular in both, circuit order kept.
  * QS_OK or QS_EPLAN.                                                        */

@@ -435,6 +435,24 @@ int64_t qs_plan_kernel_source(const qs_plan* p, uint64_t k, char* out, uint64_t 
   return (int64_t)src.size();
 }
 
+int64_t qs_plan_kernel_program(const qs_plan* p, uint64_t k, uint32_t* words, uint64_t cap, int32_t* layout) {
+  if (!p || k >= p->impl.kernels.size()) return QS_EINVAL;
+  uint64_t lk = 0;
+  const PlanImpl* Q = program_of(p, k, &lk);
+  if (lk >= Q->shm2.size() || !Q->shm2[lk].ok) return QS_EINVAL;
+  const ShmProgramV2& pg = Q->shm2[lk];
+  if (words) {
+    if (cap < pg.prog.size()) return QS_EINVAL;
+    std::copy(pg.prog.begin(), pg.prog.end(), words);
+  }
+  if (layout) {
+    layout[0] = pg.m;
+    for (int j = 0; j < kMaxShmActive; ++j) layout[1 + j] = j < pg.m ? pg.act[j] : -1;
+    for (int i = 0; i < kRegBits; ++i) layout[15 + i] = pg.load.R[i];
+  }
+  return (int64_t)pg.prog.size();
+}
+
 int qs_plan_validate(const qs_plan* p, const qs_gate* gates, uint64_t ngates) {
   if (!p) return QS_EINVAL;
   const PlanImpl& P = p->impl;

@@ -94,6 +94,7 @@ def _load():
         "qs_plan_fused_matrix": ([vp, u64, dp, u64], ctypes.c_int),
         "qs_plan_validate": ([vp, vp, u64], ctypes.c_int),
         "qs_plan_kernel_source": ([vp, u64, ctypes.c_char_p, u64], i64),
+        "qs_plan_kernel_program": ([vp, u64, ctypes.POINTER(ctypes.c_uint32), u64, ip], i64),
         "qs_state_create": ([i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "qs_alloc_state": ([i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "qs_state_free": ([vp], None),
@@ -235,6 +236,17 @@ class Plan:
         buf = ctypes.create_string_buffer(n + 1)
         check(_lib.qs_plan_kernel_source(self.h, k, buf, n + 1), "qs_plan_kernel_source")
         return buf.value.decode()
+
+    def kernel_program(self, k: int):
+        """(words, m, active qubits, load-phase slot bits) of shared-memory
+        kernel k's register-phased program (qs_plan_kernel_program)."""
+        cnt = check(_lib.qs_plan_kernel_program(self.h, k, None, 0, None), "qs_plan_kernel_program")
+        words = np.zeros(max(cnt, 1), dtype=np.uint32)
+        layout = (ctypes.c_int32 * 20)()
+        check(_lib.qs_plan_kernel_program(self.h, k, words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                          words.size, layout), "qs_plan_kernel_program")
+        m = int(layout[0])
+        return words[:cnt], m, [int(x) for x in layout[1:1 + m]], [int(x) for x in layout[15:20]]
 
     def validate(self, gates=None) -> int:
         g = self._gates if gates is None else _gates_array(gates)

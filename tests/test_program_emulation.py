@@ -1,0 +1,64 @@
+"""CPU check of the shared-memory program compiler (phase scheduling, known
+bits, gate fusion into 2x2 and 4x4 blocks, global-phase folding): every
+kernel's register-phased program, executed by a plain numpy emulator of its
+op semantics (tests/program_emulator.py), must reproduce the FP64 oracle.
+No GPU is involved; the GPU parity tests run the same programs on the
+device."""
+import numpy as np
+import pytest
+
+from oracle import sim
+from synth import circuits as C
+from tests.program_emulator import run_plan
+
+Q = pytest.importorskip("paper_2408_09055_gb300.qsim")
+
+
+def _random_state(n, seed):
+    rng = np.random.default_rng(seed)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return psi / np.linalg.norm(psi)
+
+
+CIRCUITS = {
+    "mixed": lambda n, s: C.mixed_circuit(n, 250, s),
+    "entangling": lambda n, s: C.entangling_circuit(n, 4, s),
+    "layered": lambda n, s: C.layered_u3_cz(n, 5, s),
+    "qft": lambda n, s: C.qft(n),
+}
+
+
+@pytest.mark.parametrize("kind", list(CIRCUITS))
+@pytest.mark.parametrize("algo,smax", [(2, 10), (3, 12), (3, 14), (1, 11)])
+@pytest.mark.parametrize("n", [12, 14])
+def test_programs_reproduce_the_oracle(kind, algo, smax, n):
+    g = CIRCUITS[kind](n, n + smax)
+    plan = Q.Plan(n, g, algo=algo, fuse_kmax=0, shm_max_active=smax, shm_variant=2)
+    psi0 = _random_state(n, 3 * n + smax)
+    got = run_plan(plan, n, psi0.copy())
+    ref = sim.apply(n, g, psi0.copy())
+    fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+    assert fid >= 1 - 1e-6, fid
+    assert np.max(np.abs(got - ref)) <= 1e-5
+
+
+def test_fusion_produces_dense_two_slot_blocks():
+    # the entangling circuit's CP/RXX pairs with their one-qubit gates become
+    # PK_G2 ops; the emulator above checks their values
+    n = 14
+    g = C.entangling_circuit(n, 6, 1)
+    plan = Q.Plan(n, g, fuse_kmax=0, shm_max_active=12, shm_variant=2)
+    g2 = 0
+    for k in range(plan.stats().num_kernels):
+        words, _, _, _ = plan.kernel_program(k)
+        pc = 0
+        sizes = {0: 0, 1: 9, 2: 5, 3: 5, 4: 9, 5: 1, 6: 1, 7: 1, 8: 5, 9: 3, 10: 9, 11: 9, 12: 3, 13: 9,
+                 14: 1, 15: 3, 16: 3, 18: 33}
+        while True:
+            op = int(words[pc]) & 0xFF
+            if op == 0:
+                break
+            if op == 18:
+                g2 += 1
+            pc += (1 + 5 + ((int(words[pc]) >> 8) & 0xFF)) if op == 17 else sizes[op]
+    assert g2 > 0
