@@ -23,6 +23,7 @@
 #include <sstream>
 #include <sys/stat.h>
 #include <thread>
+#include <unistd.h>
 
 #include "internal.hpp"
 #include "shm_program.hpp"
@@ -446,7 +447,12 @@ static bool compile_one(const std::string& src, std::vector<char>* cubin, std::s
   nvrtcGetCUBIN(prog, cubin->data());
   nvrtcDestroyProgram(&prog);
   mkdirs(dir);
-  const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)std::hash<std::thread::id>{}(std::this_thread::get_id()));
+  // a name no other thread or process writes (several ranks may compile the
+  // same plan at once); the rename publishes the file atomically
+  static std::atomic<unsigned> seq{0};
+  const std::string tmp = path + ".tmp." + std::to_string((long long)getpid()) + "." +
+                          std::to_string((unsigned long long)std::hash<std::thread::id>{}(std::this_thread::get_id())) +
+                          "." + std::to_string(seq.fetch_add(1));
   {
     std::ofstream f(tmp, std::ios::binary);
     f.write(cubin->data(), (std::streamsize)cubin->size());
