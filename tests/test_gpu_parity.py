@@ -180,3 +180,33 @@ def test_apply_fused_matches_kernel_unitary(k):
     Q.qs_apply_fused(buf.data_ptr(), n, targets, u, Q.QS_PREC_FP32, torch.cuda.current_stream().cuda_stream)
     got = buf.cpu().numpy().view(np.complex64)
     assert_close_state(got, ref)
+
+
+@pytest.mark.parametrize("plan_kind", ["A", "F-TF32X3"])
+def test_full_size_bench_circuit_then_adjoint(plan_kind):
+    # the bench's workload and launch configuration at full size (30 qubits,
+    # 8 GiB): the 5000-gate mixed circuit followed by its adjoint must return
+    # to |0...0>, a property that holds at any size
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 30
+    g = C.mixed_circuit(n, 5000, 100)
+    full = C.concat(g, C.adjoint(g))
+    if plan_kind == "A":
+        plan = Q.Plan(n, full, algo=3, fuse_kmax=0, shm_max_active=12)
+    else:
+        cost = Q.default_cost_table()
+        for k in range(16):
+            cost.fuse_cost[k] = 1.0
+        part = g[:600]  # fused kernels on the mixed circuit are many: a prefix keeps it short
+        full = C.concat(part, C.adjoint(part))
+        plan = Q.Plan(n, full, algo=3, fuse_kmax=6, fuse_kmin=6, precision=Q.QS_PREC_TF32X3, cost=cost)
+    s = torch.cuda.current_stream().cuda_stream
+    st = Q.State.alloc(n, s)
+    st.run(plan, s)
+    norm = st.norm2(s)  # FP64 reduction on the device
+    got = st.read(stream=s)
+    f = abs(complex(got[0])) ** 2 / norm
+    assert f >= 1 - 1e-6, f
+    got[0] = 0
+    assert float(np.max(np.abs(got))) <= 1e-5
