@@ -294,14 +294,20 @@ int qs_state_compare_c128(const qs_state* st, const double* ref_device,
 /* ---- low-level device operations (each cites its step) ------------------ */
 
 /* a6: out[pi(i)] = in[i] where pi moves bit j of i to bit perm[j]
- * (perm a permutation of 0..n-1).  Out of place; in and out must not
- * overlap.                                                                   */
+ * (perm a permutation of 0..n-1; Alg. 1's Shard).  Out of place; in and out
+ * (2^n complex64 each, device) must not overlap.  n in 1..34.  For n >= 10
+ * the call allocates its 4 KiB of index tables stream-ordered on `stream`
+ * and frees them after the launch.  Asynchronous.  Errors: QS_EINVAL (not a
+ * permutation, overlap, bad n), QS_ECUDA.                                   */
 int qs_remap(const float* in_device, float* out_device, int32_t n,
              const int32_t* perm, void* stream);
 
 /* Applies one fused 2^k x 2^k unitary (row-major complex64 on the host,
  * index bit j = qubit targets[j]) to a device state, in the given precision.
- * A direct entry to the fused-kernel path (a5).                             */
+ * A direct entry to the fused-kernel path (a5).  Tensor-core precisions
+ * widen k < 6 to 6 (identity on the added qubits) and return
+ * QS_EUNSUPPORTED for k > 6 or n < 11.  Errors: QS_EINVAL (bad targets,
+ * k outside 1..7, n outside k..34), QS_ENOMEM, QS_ECUDA.                    */
 int qs_apply_fused(float* state_device, int32_t n, const int32_t* targets,
                    int32_t k, const float* u_host, int32_t precision, void* stream);
 
