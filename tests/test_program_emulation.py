@@ -62,3 +62,36 @@ def test_fusion_produces_dense_two_slot_blocks():
                 g2 += 1
             pc += (1 + 5 + ((int(words[pc]) >> 8) & 0xFF)) if op == 17 else sizes[op]
     assert g2 > 0
+
+
+@pytest.mark.parametrize("n,L,kind", [(14, 12, "mixed"), (16, 12, "entangling"), (15, 13, "layered"),
+                                      (14, 12, "qft")])
+def test_staged_programs_reproduce_the_oracle(n, L, kind):
+    # a stage's programs address its chunk view: positions 0..L-1 are the
+    # local qubits in ascending order, L..n-1 the regional ones; running them
+    # on the whole permuted state covers every chunk (the regional bits are
+    # the batch bits above L)
+    from tests.program_emulator import run_kernel
+    g = CIRCUITS[kind](n, 7 * n + L)
+    plan = Q.Plan(n, g, fuse_kmax=0, local_qubits=L, shm_max_active=min(12, L), shm_variant=2)
+    assert plan.stats().num_stages > 1
+    psi = _random_state(n, n + L)
+    ref = sim.apply(n, g, psi.copy())
+    idx = np.arange(1 << n)
+    for si in range(plan.stats().num_stages):
+        st = plan.stage(si)
+        local = [q for q in range(n) if (st["local_mask"] >> q) & 1]
+        order = local + [q for q in range(n) if not (st["local_mask"] >> q) & 1]
+        # view index v has bit p = logical qubit order[p]
+        logical = np.zeros_like(idx)
+        for p, q in enumerate(order):
+            logical |= ((idx >> p) & 1) << q
+        view = psi[logical]
+        for k in range(st["first_kernel"], st["first_kernel"] + st["num_kernels"]):
+            words, m, act, R = plan.kernel_program(k)
+            assert max(act) < L  # every kernel stays inside the chunk
+            run_kernel(view, n, words, m, act, R)
+        psi[logical] = view
+    fid = abs(np.vdot(ref, psi)) ** 2 / (np.vdot(psi, psi).real * np.vdot(ref, ref).real)
+    assert fid >= 1 - 1e-6, fid
+    assert np.max(np.abs(psi - ref)) <= 1e-5
