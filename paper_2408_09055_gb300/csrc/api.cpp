@@ -753,6 +753,9 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
   if (reinterpret_cast<uintptr_t>(host_state) & 15) return QS_EINVAL;
   const PlanImpl& P = plan->impl;
   const int n = P.n;
+  // a staged plan of an empty circuit has no stage: nothing to apply (and
+  // the state may not fit on the device)
+  if (P.opts.local_qubits > 0 && P.opts.local_qubits < n && plan->stages.empty()) return QS_OK;
   const bool staged = !plan->stages.empty();
   const int L = staged ? P.opts.local_qubits : n;
   const uint64_t chunk_bytes = sizeof(float2) << L;

@@ -118,3 +118,11 @@ def test_host_run_rejects_bad_arguments_before_device_work():
         p.run_host(1 << 20 | 8)  # not 16-byte aligned
     assert e.value.status == -1
     assert Q._lib.qs_run_plan_host(None, None, None, 0, None) == -1
+
+
+def test_staged_empty_circuit():
+    n = 16
+    p = Q.Plan(n, C.make_gates([]), local_qubits=12, shm_max_active=12, shm_variant=2)
+    assert p.validate(C.make_gates([])) == 0
+    assert p.stats().num_kernels == 0
+    p.run_host(1 << 20)  # nothing to apply: returns before any device work
