@@ -32,7 +32,10 @@ counts and gate counts):
   perfect matching whose pairs each get CP(t1) then RXX(t2)
   (32 qubits x 40 layers = 2560 gates; also at 28 and 30 qubits).
 * ``random_subcircuit`` -- the cost-model training distribution: an active
-  set of 1..10 qubits out of 30, 1..64 gates of the mixed set acting inside it.
+  set of 1..max_active qubits out of 30 (10 by default; the cost-model
+  generator asks for up to 13, and up to 6 for fused samples), 1..64 gates
+  acting inside it, of the mixed set or of a given gate set (the generator
+  alternates the mixed set and all ten types).
 """
 from __future__ import annotations
 
