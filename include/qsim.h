@@ -158,7 +158,10 @@ typedef struct qs_kernel_desc {
   int32_t stage;      /* stage index                                        */
   int32_t nqubits;    /* |A| (shm) or k (fused), widening included          */
   int32_t num_gates;
-  uint64_t qubit_mask;/* physical qubits of A (shm) or of the fused targets */
+  uint64_t qubit_mask;/* physical qubits of A (shm) or of the fused targets;
+                         in a staged plan the circuit's qubit labels, all
+                         local to the kernel's stage (the stage's chunk view
+                         places local qubit q at its rank in local_mask)    */
   double cost;
 } qs_kernel_desc;
 int qs_plan_kernel(const qs_plan* plan, uint64_t k, qs_kernel_desc* out);

@@ -95,3 +95,78 @@ def test_staged_programs_reproduce_the_oracle(n, L, kind):
     fid = abs(np.vdot(ref, psi)) ** 2 / (np.vdot(psi, psi).real * np.vdot(ref, ref).real)
     assert fid >= 1 - 1e-6, fid
     assert np.max(np.abs(psi - ref)) <= 1e-5
+
+
+def _apply_unitary(psi, n, qubits, u):
+    # psi[.. index bit qubits[j] ..] <- sum over the target bits of u[r, c]
+    # (index bit j of r and c = qubits[j]); plain gather / matmul / scatter
+    k = len(qubits)
+    sub = np.zeros(1 << k, dtype=np.int64)
+    for j, q in enumerate(qubits):
+        sub |= ((np.arange(1 << k) >> j) & 1) << q
+    rest = [q for q in range(n) if q not in qubits]
+    base = np.zeros(1 << (n - k), dtype=np.int64)
+    for j, q in enumerate(rest):
+        base |= ((np.arange(1 << (n - k)) >> j) & 1) << q
+    idx = base[:, None] | sub[None, :]
+    psi[idx] = psi[idx] @ u.T
+
+
+def _run_mixed(plan, n, psi, kernels, qubit_pos):
+    from tests.program_emulator import run_kernel
+    for k in kernels:
+        d = plan.kernel(k)
+        if d.type == Q.QS_KERNEL_FUSED:
+            qubits = [qubit_pos[q] for q in range(n) if (d.qubit_mask >> q) & 1]
+            _apply_unitary(psi, n, qubits, plan.fused_matrix(k))
+        else:
+            words, m, act, R = plan.kernel_program(k)
+            run_kernel(psi, n, words, m, act, R)
+
+
+@pytest.mark.parametrize("kind", list(CIRCUITS))
+@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("n,L", [(14, 0), (16, 0), (14, 12), (16, 12)])
+def test_mixed_plans_reproduce_the_oracle(kind, precision, n, L):
+    # fusion made cheap enough that the planner mixes fused and shared-memory
+    # kernels: the fused kernels' FP64 unitaries (widened to six targets for
+    # the tensor-core precisions) and the programs, applied in plan order,
+    # must reproduce the oracle; staged plans run on the stage's chunk view
+    g = CIRCUITS[kind](n, 5 * n + L + precision)
+    cost = Q.default_cost_table()
+    for k in range(16):
+        cost.fuse_cost[k] *= 0.3
+    kw = dict(precision=precision, shm_max_active=12, shm_variant=2, cost=cost)
+    if L:
+        kw["local_qubits"] = L
+    plan = Q.Plan(n, g, **kw)
+    psi = _random_state(n, 11 * n + L + precision)
+    ref = sim.apply(n, g, psi.copy())
+    s = plan.stats()
+    if not L:
+        _run_mixed(plan, n, psi, range(s.num_kernels), list(range(n)))
+    else:
+        idx = np.arange(1 << n)
+        for si in range(s.num_stages):
+            st = plan.stage(si)
+            local = [q for q in range(n) if (st["local_mask"] >> q) & 1]
+            order = local + [q for q in range(n) if not (st["local_mask"] >> q) & 1]
+            logical = np.zeros_like(idx)
+            for p, q in enumerate(order):
+                logical |= ((idx >> p) & 1) << q
+            pos = {q: p for p, q in enumerate(order)}
+            view = psi[logical]
+            ks = range(st["first_kernel"], st["first_kernel"] + st["num_kernels"])
+            for k in ks:
+                d = plan.kernel(k)
+                assert d.qubit_mask & ~st["local_mask"] == 0  # inside the chunk
+            _run_mixed(plan, n, view, ks, pos)
+            psi[logical] = view
+    if precision:
+        for k in range(s.num_kernels):
+            d = plan.kernel(k)
+            if d.type == Q.QS_KERNEL_FUSED:
+                assert d.nqubits >= min(6, n) and plan.fused_matrix(k).shape == (1 << d.nqubits,) * 2
+    fid = abs(np.vdot(ref, psi)) ** 2 / (np.vdot(psi, psi).real * np.vdot(ref, ref).real)
+    assert fid >= 1 - 1e-6, fid
+    assert np.max(np.abs(psi - ref)) <= 1e-5
