@@ -10,10 +10,11 @@
 // every choice when there are at most kMaxChoices of them (otherwise the
 // local set grows in circuit order until the next gate no longer fits and
 // the free slots go to the qubits the remaining gates need first), and a beam
-// search keeps several of the best partial stagings so that a stage that
-// takes slightly fewer gates can still lead to fewer stages overall.  Gates on disjoint qubits
+// search keeps many partial stagings so that a stage that takes fewer gates
+// can still lead to fewer stages overall.  Gates on disjoint qubits
 // commute, so a stage takes every gate whose non-insular qubits are local
 // and that shares no qubit with an earlier gate left for a later stage.
+#include <algorithm>
 #include <bit>
 #include <numeric>
 
@@ -114,50 +115,78 @@ std::vector<std::pair<size_t, uint64_t>> stage_choices(const std::vector<Gate>& 
   return out;
 }
 
-// Beam search over stage sequences: every partial staging keeps its
-// remaining gates; each step expands the kBeam partial stagings that covered
-// the most gates by their kExpand best local sets.  All partial stagings of
-// a step have the same number of stages, so the first to cover every gate
-// uses the fewest stages the search saw (greedy, one set per stage, is the
-// width-1 case).
-constexpr int kBeam = 6, kExpand = 6;
+// Beam search over stage sequences.  Every partial staging keeps its
+// remaining gates and the qubits that became local at its stage boundaries
+// (the objective of Sec. 4's ILP with no global qubits).  Each step expands
+// every partial staging by every local set that takes a gate and keeps the
+// `width` best children with distinct remaining gates: fewest gates left, then
+// the least objective.  The first stage that takes the most gates need not
+// be on a shortest staging, so the children are not limited to the best
+// few sets of their parent.  All partial stagings of a step have the same
+// number of stages, so the first step that covers every gate uses the
+// fewest stages the search saw, and of those it takes the least objective.
+// The width shrinks as the sets per stage grow (about 2^16 children a step).
+constexpr int kMaxBeam = 64, kMinBeam = 6;
+constexpr uint64_t kChildrenPerStep = 1u << 16;
+constexpr int kScanPerKept = 16;  // children tried per kept one when removing duplicates
 
 std::vector<uint64_t> choose_local_sets(const std::vector<Gate>& g, const std::vector<int32_t>& rest0, int n,
                                         int L, int jlow, uint64_t low, uint64_t all) {
+  const uint64_t nsets = std::min<uint64_t>(binom(n - jlow, n - L), kMaxChoices + 1);
+  const int width = (int)std::clamp<uint64_t>(kChildrenPerStep / std::max<uint64_t>(nsets, 1), kMinBeam, kMaxBeam);
   struct Partial {
     std::vector<int32_t> rest;
     std::vector<uint64_t> sets;
+    int cost = 0;
+  };
+  struct Child {
+    size_t left;    // gates still to stage
+    int cost;       // qubits made local so far
+    size_t parent;  // index into the beam
+    uint64_t S;     // the stage's local set
   };
   std::vector<Partial> beam(1);
   beam[0].rest = rest0;
   while (true) {
-    std::vector<Partial> next;
-    for (const Partial& p : beam) {
-      const auto ch = stage_choices(g, p.rest, n, L, jlow, low, all);
-      for (size_t k = 0; k < ch.size() && k < (size_t)kExpand; ++k) {
-        if (ch[k].first == 0) break;
-        Partial c;
-        c.sets = p.sets;
-        c.sets.push_back(ch[k].second);
-        admitted(g, p.rest, ch[k].second, all, nullptr, &c.rest);
-        if (c.rest.empty()) return c.sets;
-        next.push_back(std::move(c));
+    // every child, scored without materialising its remaining gates
+    std::vector<Child> next;
+    for (size_t b = 0; b < beam.size(); ++b) {
+      const Partial& p = beam[b];
+      const uint64_t prev = p.sets.empty() ? 0 : p.sets.back();
+      for (const auto& [taken, S] : stage_choices(g, p.rest, n, L, jlow, low, all)) {
+        if (taken == 0) break;  // ranked: no later set takes a gate
+        const int c = p.sets.empty() ? 0 : p.cost + std::popcount(S & ~prev);
+        next.push_back({p.rest.size() - taken, c, b, S});
       }
     }
     if (next.empty()) return {};
-    std::stable_sort(next.begin(), next.end(),
-                     [](const Partial& a, const Partial& b) { return a.rest.size() < b.rest.size(); });
+    std::stable_sort(next.begin(), next.end(), [](const Child& a, const Child& b) {
+      return a.left != b.left ? a.left < b.left : a.cost < b.cost;
+    });
+    if (next[0].left == 0) {  // complete: the least objective among the shortest
+      std::vector<uint64_t> sets = beam[next[0].parent].sets;
+      sets.push_back(next[0].S);
+      return sets;
+    }
     // distinct remaining sets only (different choices often leave the same gates)
     std::vector<Partial> keep;
-    for (Partial& c : next) {
+    const size_t scan = std::min(next.size(), (size_t)width * kScanPerKept);
+    for (size_t i = 0; i < scan; ++i) {
+      const Child& c = next[i];
+      Partial q;
+      admitted(g, beam[c.parent].rest, c.S, all, nullptr, &q.rest);
       bool dup = false;
       for (const Partial& k : keep)
-        if (k.rest == c.rest) {
+        if (k.rest == q.rest) {
           dup = true;
           break;
         }
-      if (!dup) keep.push_back(std::move(c));
-      if ((int)keep.size() == kBeam) break;
+      if (dup) continue;
+      q.sets = beam[c.parent].sets;
+      q.sets.push_back(c.S);
+      q.cost = c.cost;
+      keep.push_back(std::move(q));
+      if ((int)keep.size() == width) break;
     }
     beam.swap(keep);
   }
