@@ -176,6 +176,8 @@ def default_opts(**kw) -> qs_plan_opts:
     if kw.get("mlp") is not None:
         o.mlp = kw["mlp"].h.value
         o.cost_kind = QS_COST_LEARNED
+    # the options hold raw pointers: keep their owners alive with them
+    o._owners = (kw.get("cost"), kw.get("mlp"))
     return o
 
 
@@ -192,7 +194,6 @@ class Plan:
         g = _gates_array(gates)
         self._gates = g
         self.opts = opts if opts is not None else default_opts(**kw)
-        self._keep = self.opts.cost  # keep the cost table alive
         h = ctypes.c_void_p()
         check(_lib.qs_plan_circuit(int(n), g.ctypes.data_as(ctypes.c_void_p), len(g),
                                    ctypes.byref(self.opts), ctypes.byref(h)), "qs_plan_circuit")
