@@ -79,6 +79,16 @@ enum qs_precision {
   QS_PREC_TF32X3 = 2  /* split-precision 3xTF32 on tensor cores              */
 };
 enum qs_kernel_type { QS_KERNEL_SHM = 0, QS_KERNEL_FUSED = 1 };
+/* How a staged plan chooses its local sets (Sec. 4).  Both keep the
+ * L - 8 lowest qubits local and give each stage every gate it can take. */
+enum qs_stager {
+  QS_STAGER_BEAM = 0,  /* beam search over local-set sequences: fewest gates
+                          left, then the least objective (default)           */
+  QS_STAGER_EXACT = 1  /* branch and bound from the beam's staging: the fewest
+                          stages, then the least objective -- what the ILP of
+                          Sec. 4 returns (Theorem 1) -- when the search ends
+                          within stager_budget; else the best staging found */
+};
 
 /* Analytic cost ("Cost Function in Kernelize"): a shared-memory kernel costs
  * alpha + sum of gate_cost[type]; a fused kernel on k qubits costs
@@ -118,10 +128,14 @@ typedef struct qs_plan_opts {
                              per plan (NVRTC, sm_103a)                         */
   const qs_cost_table* cost; /* NULL: built-in table                           */
   const qs_mlp* mlp;         /* learned cost model (cost_kind = LEARNED)        */
+  int64_t stager_budget;  /* QS_STAGER_EXACT: work limit in gate visits
+                             (<= 0: 2^28, about a second)                     */
+  int32_t stager;         /* enum qs_stager (staged plans only)                */
 } qs_plan_opts;
 
 /* Fills `opts` with the defaults (Kernelize, analytic cost, FP32, |A| <= 13,
- * 4 forced low qubits, fused k in [1, 6], T = 500, attach on, L = n).       */
+ * 4 forced low qubits, fused k in [1, 6], T = 500, attach on, L = n, beam
+ * stager).                                                                  */
 void qs_plan_opts_default(qs_plan_opts* opts);
 /* The built-in analytic cost table. */
 void qs_cost_table_default(qs_cost_table* out);
@@ -150,6 +164,10 @@ typedef struct qs_plan_stats {
   uint64_t num_exchanges; /* shared-memory exchanges summed over those       */
   uint64_t num_jit;       /* of those, kernels specialised per plan (NVRTC)  */
   double jit_ms;          /* host time compiling them (included in planner_ms) */
+  int32_t staging_cost;   /* the objective of Sec. 4 with no global qubits:
+                             qubits that become local at stage boundaries    */
+  int32_t staging_optimal;/* 1 when the exact stager proved the staging has
+                             the fewest stages and then the least objective */
 } qs_plan_stats;
 int qs_plan_stats_get(const qs_plan* plan, qs_plan_stats* out);
 

@@ -168,6 +168,8 @@ void qs_plan_opts_default(qs_plan_opts* o) {
   o->shm_variant = 0;
   o->cost = nullptr;
   o->mlp = nullptr;
+  o->stager_budget = 0;
+  o->stager = QS_STAGER_BEAM;
 }
 
 }  // extern "C"
@@ -201,7 +203,7 @@ static int build_impl(PlanImpl& P, int n, const qs_gate* gates, const int32_t* i
 static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o) {
   PlanImpl& P = p->impl;
   const int n = P.n, L = o.local_qubits;
-  int rc = stage_circuit(P.gates, n, L, &p->stages);
+  int rc = stage_circuit(P.gates, n, L, o.stager, o.stager_budget, &p->stages, &p->staging_optimal);
   if (rc != QS_OK) return rc;
   for (size_t si = 0; si < p->stages.size(); ++si) {
     Stage& st = p->stages[si];
@@ -288,6 +290,7 @@ int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_p
   if (o.cost_kind != QS_COST_ANALYTIC && o.cost_kind != QS_COST_LEARNED) return QS_EINVAL;
   if (o.shm_variant < 0 || o.shm_variant > 3) return QS_EINVAL;
   if (o.local_qubits < 0) return QS_EINVAL;
+  if (o.stager != QS_STAGER_BEAM && o.stager != QS_STAGER_EXACT) return QS_EINVAL;
   if (o.local_qubits >= n) o.local_qubits = 0;
   const bool staged = o.local_qubits > 0;
   // a chunk holds the widest kernel (a 2^14 tile, a widened fused kernel)
@@ -372,6 +375,10 @@ int qs_plan_stats_get(const qs_plan* p, qs_plan_stats* s) {
   if (p->stages.empty()) count(P);
   for (const auto& st : p->stages) count(*st.plan);
   s->jit_ms = P.jit_ms;
+  std::vector<uint64_t> sets;
+  for (const auto& st : p->stages) sets.push_back(st.local);
+  s->staging_cost = staging_objective(sets);
+  s->staging_optimal = p->staging_optimal ? 1 : 0;
   return QS_OK;
 }
 

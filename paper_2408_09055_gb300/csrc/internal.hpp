@@ -173,10 +173,15 @@ struct Stage {
 // local qubits the stager may choose freely; the rest, L - kStageSlots
 // lowest qubits, stay local in every stage so host runs are 2^(L-8) long
 constexpr int kStageSlots = 8;
-constexpr int kMinLocalQubits = 12;
+constexpr int kMinLocalQubits = 12;  // a chunk holds a 2^12 tile and a tensor-core kernel
 constexpr int kMaxChunkBuffers = 4;  // chunks in flight: copy-in, kernels, copy-out, slack
-constexpr uint64_t kMaxHostTimerRecords = 1ull << 16;  // stages x chunks of a timed host run  // a chunk holds a 2^12 tile and a tensor-core kernel
-int stage_circuit(const std::vector<Gate>& gates, int n, int L, std::vector<Stage>* out);
+constexpr uint64_t kMaxHostTimerRecords = 1ull << 16;  // stages x chunks of a timed host run
+constexpr int64_t kDefaultStagerBudget = 1ll << 28;  // gate visits of the exact stager
+// Stages the circuit (QS_STAGER_BEAM or QS_STAGER_EXACT); *optimal is set
+// when the exact search finished.
+int stage_circuit(const std::vector<Gate>& gates, int n, int L, int stager, int64_t budget,
+                  std::vector<Stage>* out, bool* optimal);
+int staging_objective(const std::vector<uint64_t>& sets);
 
 // ---- device side (kernels_*.cu) ----------------------------------------------
 struct ShmLaunch {
@@ -230,6 +235,7 @@ void set_cuda_error(const char* what, cudaError_t e);
 struct qs_plan {
   qs::PlanImpl impl;  // staged plans: the gates and the flattened kernel list
   std::vector<qs::Stage> stages;  // empty unless local_qubits < n
+  bool staging_optimal = false;   // the exact stager finished its search
   std::vector<std::pair<int32_t, int32_t>> kmap;  // flattened kernel -> (stage, kernel)
 };
 struct qs_state {

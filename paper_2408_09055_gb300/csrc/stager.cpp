@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <bit>
 #include <numeric>
+#include <unordered_map>
 
 #include "internal.hpp"
 
@@ -192,8 +193,130 @@ std::vector<uint64_t> choose_local_sets(const std::vector<Gate>& g, const std::v
   }
 }
 
-int stage_circuit(const std::vector<Gate>& g, int n, int L, std::vector<Stage>* out) {
+// The objective of Sec. 4's ILP with no global qubits: qubits that become
+// local from one stage to the next.
+int staging_objective(const std::vector<uint64_t>& sets) {
+  int c = 0;
+  for (size_t k = 1; k < sets.size(); ++k) c += std::popcount(sets[k] & ~sets[k - 1]);
+  return c;
+}
+
+namespace {
+
+// Branch and bound over local-set sequences for the fewest stages and then
+// the least objective, the two things the ILP of Sec. 4 optimises (Theorem
+// 1).  Each stage takes every gate its local set admits: a larger finished
+// set never hurts later stages, so that loses no staging.  Bounds at a
+// partial staging with remaining gates R, last local set P and d stages:
+// the non-insular qubits U of R outside the always-local ones need at least
+// ceil(|U| / free slots) more stages, and every qubit of U not in P must
+// still become local once.  A partial staging is also dropped when one with
+// the same remaining gates and last set was reached with no more stages and
+// no more objective.
+class ExactStager {
+  static constexpr uint64_t kNodeCharge = 256;
+
+ public:
+  ExactStager(const std::vector<Gate>& g, int n, int L, int jlow, uint64_t low, uint64_t all, int64_t budget)
+      : g_(g), n_(n), L_(L), jlow_(jlow), low_(low), all_(all), budget_(budget) {}
+
+  // `best`: the incumbent staging on entry, the best found on return.  True
+  // when the search ran to the end (the result is optimal).
+  bool run(const std::vector<int32_t>& rest0, std::vector<uint64_t>* best) {
+    best_ = *best;
+    best_s_ = (int)best_.size();
+    best_cost_ = staging_objective(best_);
+    dfs(rest0, 0, 0, 0);
+    *best = best_;
+    return !out_;
+  }
+
+ private:
+  struct Key {
+    uint64_t h1, h2, last;
+    bool operator==(const Key& o) const { return h1 == o.h1 && h2 == o.h2 && last == o.last; }
+  };
+  struct KeyHash {
+    size_t operator()(const Key& k) const { return (size_t)(k.h1 ^ (k.h2 * 0x9E3779B97F4A7C15ull) ^ k.last); }
+  };
+
+  static Key key_of(const std::vector<int32_t>& rest, uint64_t last) {
+    uint64_t h1 = 1469598103934665603ull, h2 = 0x2545F4914F6CDD1Dull;  // FNV-1a and a multiply-xorshift
+    for (int32_t i : rest) {
+      h1 = (h1 ^ (uint64_t)(uint32_t)i) * 1099511628211ull;
+      h2 = (h2 + (uint64_t)(uint32_t)i + 1) * 0xBF58476D1CE4E5B9ull;
+      h2 ^= h2 >> 31;
+    }
+    return {h1, h2, last};
+  }
+
+  bool spend(uint64_t w) {
+    budget_ -= (int64_t)w;
+    if (budget_ < 0) out_ = true;
+    return !out_;
+  }
+
+  // rest: gates left; last: the previous stage's local set; cost: the
+  // objective of the stages so far
+  void dfs(const std::vector<int32_t>& rest, uint64_t last, int depth, int cost) {
+    if (out_) return;
+    if (rest.empty()) {
+      if (depth < best_s_ || (depth == best_s_ && cost < best_cost_)) {
+        best_ = cur_;
+        best_s_ = depth;
+        best_cost_ = cost;
+      }
+      return;
+    }
+    uint64_t U = 0;
+    for (int32_t i : rest) U |= g_[i].nimask;
+    U &= ~low_;
+    const int slots = L_ - jlow_;
+    const int more = std::max(1, (std::popcount(U) + slots - 1) / slots);
+    const int lb_cost = depth == 0 ? std::max(0, std::popcount(U) - slots) : cost + std::popcount(U & ~last);
+    if (depth + more > best_s_ || (depth + more == best_s_ && lb_cost >= best_cost_)) return;
+    const Key k = key_of(rest, last);
+    auto it = seen_.find(k);
+    if (it != seen_.end() && it->second.first <= depth && it->second.second <= cost) return;
+    seen_[k] = {depth, cost};
+    // a node's memo entry is charged too, which bounds the memo's size
+    if (!spend(kNodeCharge + (uint64_t)rest.size() * nsets())) return;
+    auto ch = stage_choices(g_, rest, n_, L_, jlow_, low_, all_);
+    // most gates first, then the fewest new local qubits
+    std::stable_sort(ch.begin(), ch.end(), [&](const auto& a, const auto& b) {
+      if (a.first != b.first) return a.first > b.first;
+      return depth > 0 && std::popcount(a.second & ~last) < std::popcount(b.second & ~last);
+    });
+    for (const auto& [taken, S] : ch) {
+      if (taken == 0 || out_) break;
+      std::vector<int32_t> left;
+      left.reserve(rest.size() - taken);
+      if (!spend(rest.size())) return;
+      admitted(g_, rest, S, all_, nullptr, &left);
+      cur_.push_back(S);
+      dfs(left, S, depth + 1, cost + (depth > 0 ? std::popcount(S & ~last) : 0));
+      cur_.pop_back();
+    }
+  }
+
+  uint64_t nsets() const { return std::max<uint64_t>(1, binom(n_ - jlow_, n_ - L_)); }
+
+  const std::vector<Gate>& g_;
+  int n_, L_, jlow_;
+  uint64_t low_, all_;
+  int64_t budget_;
+  bool out_ = false;
+  std::vector<uint64_t> best_, cur_;
+  int best_s_ = 0, best_cost_ = 0;
+  std::unordered_map<Key, std::pair<int, int>, KeyHash> seen_;
+};
+
+}  // namespace
+
+int stage_circuit(const std::vector<Gate>& g, int n, int L, int stager, int64_t budget, std::vector<Stage>* out,
+                  bool* optimal) {
   out->clear();
+  *optimal = false;
   if (L < 2 || L > n) return QS_EINVAL;
   const int jlow = std::max(0, L - kStageSlots);
   const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;
@@ -202,8 +325,13 @@ int stage_circuit(const std::vector<Gate>& g, int n, int L, std::vector<Stage>* 
   std::iota(rest.begin(), rest.end(), 0);
   for (const Gate& x : g)
     if (std::popcount(low | x.nimask) > L) return QS_EPLAN;
-  // the local sets of all stages, by a beam search over the greedy choices
-  const std::vector<uint64_t> plan = choose_local_sets(g, rest, n, L, jlow, low, all);
+  // the local sets of all stages, by a beam search over the greedy choices,
+  // improved by the exact search when asked for and every set can be tried
+  std::vector<uint64_t> plan = choose_local_sets(g, rest, n, L, jlow, low, all);
+  if (stager == QS_STAGER_EXACT && !plan.empty() && binom(n - jlow, n - L) <= kMaxChoices) {
+    ExactStager ex(g, n, L, jlow, low, all, budget > 0 ? budget : kDefaultStagerBudget);
+    *optimal = ex.run(rest, &plan);
+  }
   size_t next = 0;
   while (!rest.empty()) {
     if (next >= plan.size()) return QS_EPLAN;

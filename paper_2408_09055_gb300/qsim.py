@@ -20,6 +20,7 @@ QS_ALGO_PER_GATE, QS_ALGO_GREEDY, QS_ALGO_ORDERED, QS_ALGO_KERNELIZE = 0, 1, 2, 
 QS_COST_ANALYTIC, QS_COST_LEARNED = 0, 1
 QS_PREC_FP32, QS_PREC_TF32, QS_PREC_TF32X3 = 0, 1, 2
 QS_KERNEL_SHM, QS_KERNEL_FUSED = 0, 1
+QS_STAGER_BEAM, QS_STAGER_EXACT = 0, 1
 QS_MLP_FEATURES = 44
 NUM_GATE_TYPES = 10
 
@@ -51,7 +52,8 @@ class qs_plan_opts(ctypes.Structure):
                 ("fuse_kmax", ctypes.c_int32), ("prune_T", ctypes.c_int32),
                 ("attach_single", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
                 ("shm_variant", ctypes.c_int32),
-                ("cost", ctypes.POINTER(qs_cost_table)), ("mlp", ctypes.c_void_p)]
+                ("cost", ctypes.POINTER(qs_cost_table)), ("mlp", ctypes.c_void_p),
+                ("stager_budget", ctypes.c_int64), ("stager", ctypes.c_int32)]
 
 
 class qs_plan_stats(ctypes.Structure):
@@ -61,7 +63,8 @@ class qs_plan_stats(ctypes.Structure):
                 ("cost", ctypes.c_double), ("planner_ms", ctypes.c_double),
                 ("dp_states", ctypes.c_uint64), ("num_phased", ctypes.c_uint64),
                 ("num_exchanges", ctypes.c_uint64), ("num_jit", ctypes.c_uint64),
-                ("jit_ms", ctypes.c_double)]
+                ("jit_ms", ctypes.c_double), ("staging_cost", ctypes.c_int32),
+                ("staging_optimal", ctypes.c_int32)]
 
 
 class qs_kernel_desc(ctypes.Structure):

@@ -36,3 +36,36 @@ def test_status_strings_and_defaults_without_gpu():
     assert Q.lib.qs_strerror(Q.QS_EINVAL) == b"invalid argument"
     o = Q.default_opts()
     assert o.shm_max_active == 13 and o.forced_low == 4 and o.prune_T == 500 and o.algo == Q.QS_ALGO_KERNELIZE
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # sizeof and every field offset of the header's structs, from a C
+    # compiler, against the ctypes mirrors in the binding
+    import shutil
+    import subprocess
+    from paper_2408_09055_gb300 import qsim as Q
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [Q.qs_gate, Q.qs_cost_table, Q.qs_plan_opts, Q.qs_plan_stats, Q.qs_kernel_desc]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "qsim.h"', "int main(void) {"]
+    for S in structs:
+        name = S.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in S._fields_:
+            lines.append(f'  printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                              text=True).stdout.splitlines())
+    for S in structs:
+        assert int(got[S.__name__]) == ctypes.sizeof(S), S.__name__
+        for f in S._fields_:
+            assert int(got[f"{S.__name__}.{f[0]}"]) == getattr(S, f[0]).offset, f"{S.__name__}.{f[0]}"
+    # every field the header declares is mirrored: C size = ctypes size above,
+    # and the default options fill the stager fields
+    o = Q.default_opts()
+    assert o.stager == Q.QS_STAGER_BEAM and o.stager_budget == 0

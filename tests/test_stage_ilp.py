@@ -83,3 +83,48 @@ def test_library_stager_reaches_the_ilp_stage_count(kind, n, L, size, seed):
     s, cost, _ = SI.stage(g, n, L, fixed_local=range(max(0, L - 8)))
     assert ours == s
     assert our_cost >= cost  # the ILP's objective is optimal for that count
+
+
+def _make(kind, n, size, seed):
+    return {"mixed": lambda: C.mixed_circuit(n, size, seed), "layered": lambda: C.layered_u3_cz(n, size, seed),
+            "entangling": lambda: C.entangling_circuit(n, size, seed), "qft": lambda: C.qft(n)}[kind]()
+
+
+@pytest.mark.parametrize("kind,n,L,size,seed", CASES)
+def test_exact_stager_equals_the_ilp(kind, n, L, size, seed):
+    # Theorem 1: the fewest stages, and at that count the ILP's objective;
+    # the exact stager proves both within its default budget here
+    g = _make(kind, n, size, seed)
+    p = Q.Plan(n, g, local_qubits=L, shm_max_active=12, fuse_kmax=0, shm_variant=1, stager=Q.QS_STAGER_EXACT)
+    st = p.stats()
+    assert st.staging_optimal == 1
+    s, cost, _ = SI.stage(g, n, L, fixed_local=range(max(0, L - 8)))
+    assert (st.num_stages, st.staging_cost) == (s, cost)
+    assert p.validate() == 0
+    masks = [p.stage(k)["local_mask"] for k in range(st.num_stages)]
+    assert all(m & ((1 << (L - 8)) - 1) == (1 << (L - 8)) - 1 for m in masks)
+
+
+def test_exact_stager_out_of_budget_keeps_the_beam_staging():
+    g = C.mixed_circuit(16, 120, 3)
+    beam = Q.Plan(16, g, local_qubits=12, shm_max_active=12, fuse_kmax=0, shm_variant=1)
+    cut = Q.Plan(16, g, local_qubits=12, shm_max_active=12, fuse_kmax=0, shm_variant=1,
+                 stager=Q.QS_STAGER_EXACT, stager_budget=1)
+    assert cut.stats().staging_optimal == 0 and beam.stats().staging_optimal == 0
+    assert [s["local_mask"] for s in cut.stages()] == [s["local_mask"] for s in beam.stages()]
+    assert cut.stats().staging_cost == beam.stats().staging_cost
+
+
+def test_staging_cost_counts_new_local_qubits():
+    g = C.mixed_circuit(16, 200, 9)
+    p = Q.Plan(16, g, local_qubits=12, shm_max_active=12, fuse_kmax=0, shm_variant=1)
+    m = [s["local_mask"] for s in p.stages()]
+    assert p.stats().staging_cost == sum(bin(m[k] & ~m[k - 1]).count("1") for k in range(1, len(m)))
+    # unstaged plans have no boundary
+    assert Q.Plan(16, g, shm_variant=1).stats().staging_cost == 0
+
+
+def test_unknown_stager_is_rejected():
+    with pytest.raises(Q.QsError) as e:
+        Q.Plan(16, C.mixed_circuit(16, 50, 1), local_qubits=12, shm_max_active=12, stager=7)
+    assert e.value.status == Q.QS_EINVAL
