@@ -411,6 +411,7 @@ def staged_measure(args):
                                f"host memory",
                    "n_qubits": n, "local_qubits": L, "gates": int(len(gates)), "stages": int(ps.num_stages),
                    "kernels": int(ps.num_kernels), "chunk_buffers": nbuf, "planner_s": plan_s,
+                   "stager": "beam", "staging_objective": int(ps.staging_cost),
                    "plan": "analytic-cost Kernelize per stage, shared-memory kernels, FP32"},
         "roofline": {"bound": "c2c", "achieved": achieved, "peak": peaks_c["both"], "unit": "GB/s",
                      "frac": achieved / peaks_c["both"], "traffic": moved,

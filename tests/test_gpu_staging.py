@@ -63,6 +63,20 @@ def test_staged_plans_match_oracle(case, nbuf):
     assert_close_state(got, sim.apply(n, g))
 
 
+def test_exact_stager_plan_matches_oracle():
+    # the exact stager's local sets through the same chunked executor
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n, L = 16, 12
+    g = C.mixed_circuit(n, 120, 3)
+    plan = Q.Plan(n, g, local_qubits=L, shm_max_active=12, stager=Q.QS_STAGER_EXACT)
+    st = plan.stats()
+    assert st.staging_optimal == 1 and st.num_stages > 1 and plan.validate() == 0
+    psi0 = random_state(n, 17)
+    got = run_host(plan, n, psi0, nbuf=2)
+    assert_close_state(got, sim.apply(n, g, psi0.copy()))
+
+
 @pytest.mark.parametrize("variant,nbuf", [(1, 2), (2, 3), (3, 4), (3, 1)])
 def test_staged_random_initial_state(variant, nbuf):
     # every amplitude nonzero: a chunk gathered or scattered to the wrong
