@@ -85,9 +85,9 @@ enum qs_stager {
   QS_STAGER_BEAM = 0,  /* beam search over local-set sequences: fewest gates
                           left, then the least objective (default)           */
   QS_STAGER_EXACT = 1  /* branch and bound from the beam's staging: the fewest
-                          stages, then the least objective -- what the ILP of
-                          Sec. 4 returns (Theorem 1) -- when the search ends
-                          within stager_budget; else the best staging found */
+                          stages (Theorem 1), then the least objective at that
+                          count -- what the ILP of Sec. 4 returns -- as far as
+                          stager_budget allows; else the best staging found */
 };
 
 /* Analytic cost ("Cost Function in Kernelize"): a shared-memory kernel costs
@@ -166,8 +166,9 @@ typedef struct qs_plan_stats {
   double jit_ms;          /* host time compiling them (included in planner_ms) */
   int32_t staging_cost;   /* the objective of Sec. 4 with no global qubits:
                              qubits that become local at stage boundaries    */
-  int32_t staging_optimal;/* 1 when the exact stager proved the staging has
-                             the fewest stages and then the least objective */
+  int32_t staging_optimal;/* exact stager: 1 when it proved the fewest
+                             stages, 2 when also the least objective at that
+                             count; 0 otherwise                              */
 } qs_plan_stats;
 int qs_plan_stats_get(const qs_plan* plan, qs_plan_stats* out);
 

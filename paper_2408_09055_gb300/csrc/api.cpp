@@ -378,7 +378,7 @@ int qs_plan_stats_get(const qs_plan* p, qs_plan_stats* s) {
   std::vector<uint64_t> sets;
   for (const auto& st : p->stages) sets.push_back(st.local);
   s->staging_cost = staging_objective(sets);
-  s->staging_optimal = p->staging_optimal ? 1 : 0;
+  s->staging_optimal = p->staging_optimal;
   return QS_OK;
 }
 

@@ -177,10 +177,10 @@ constexpr int kMinLocalQubits = 12;  // a chunk holds a 2^12 tile and a tensor-c
 constexpr int kMaxChunkBuffers = 4;  // chunks in flight: copy-in, kernels, copy-out, slack
 constexpr uint64_t kMaxHostTimerRecords = 1ull << 16;  // stages x chunks of a timed host run
 constexpr int64_t kDefaultStagerBudget = 1ll << 28;  // gate visits of the exact stager
-// Stages the circuit (QS_STAGER_BEAM or QS_STAGER_EXACT); *optimal is set
-// when the exact search finished.
+// Stages the circuit (QS_STAGER_BEAM or QS_STAGER_EXACT); *optimal: 1 when
+// the exact search proved the fewest stages, 2 when also the least objective.
 int stage_circuit(const std::vector<Gate>& gates, int n, int L, int stager, int64_t budget,
-                  std::vector<Stage>* out, bool* optimal);
+                  std::vector<Stage>* out, int* optimal);
 int staging_objective(const std::vector<uint64_t>& sets);
 
 // ---- device side (kernels_*.cu) ----------------------------------------------
@@ -235,7 +235,7 @@ void set_cuda_error(const char* what, cudaError_t e);
 struct qs_plan {
   qs::PlanImpl impl;  // staged plans: the gates and the flattened kernel list
   std::vector<qs::Stage> stages;  // empty unless local_qubits < n
-  bool staging_optimal = false;   // the exact stager finished its search
+  int staging_optimal = 0;  // 1: fewest stages proven, 2: and the least objective
   std::vector<std::pair<int32_t, int32_t>> kmap;  // flattened kernel -> (stage, kernel)
 };
 struct qs_state {

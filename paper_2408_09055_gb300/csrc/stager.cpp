@@ -220,15 +220,31 @@ class ExactStager {
   ExactStager(const std::vector<Gate>& g, int n, int L, int jlow, uint64_t low, uint64_t all, int64_t budget)
       : g_(g), n_(n), L_(L), jlow_(jlow), low_(low), all_(all), budget_(budget) {}
 
-  // `best`: the incumbent staging on entry, the best found on return.  True
-  // when the search ran to the end (the result is optimal).
-  bool run(const std::vector<int32_t>& rest0, std::vector<uint64_t>* best) {
+  // `best`: the incumbent staging on entry, the best found on return.
+  // Returns 0 when the budget ran out first, 1 when the fewest stages are
+  // proven, 2 when the least objective at that count is proven too.
+  int run(const std::vector<int32_t>& rest0, std::vector<uint64_t>* best) {
     best_ = *best;
     best_s_ = (int)best_.size();
     best_cost_ = staging_objective(best_);
-    dfs(rest0, 0, 0, 0);
+    // phase 1, the stage count (Theorem 1): look for a staging one stage
+    // shorter than the incumbent until there is none
+    while (!out_) {
+      cur_.clear();
+      if (!shorter(rest0, 0, best_s_ - 1)) break;
+      best_ = cur_;
+      best_s_ = (int)best_.size();
+      best_cost_ = staging_objective(best_);
+    }
+    int proven = out_ ? 0 : 1;
+    // phase 2, the objective at that count
+    if (!out_) {
+      cur_.clear();
+      dfs(rest0, 0, 0, 0);
+      if (!out_) proven = 2;
+    }
     *best = best_;
-    return !out_;
+    return proven;
   }
 
  private:
@@ -250,6 +266,49 @@ class ExactStager {
     return {h1, h2, last};
   }
 
+  // The lower bound on the stages still needed for `rest`: the non-insular
+  // qubits it needs beyond the always-local ones, `slots` per stage.
+  int more_stages(const std::vector<int32_t>& rest, uint64_t* U_out) const {
+    uint64_t U = 0;
+    for (int32_t i : rest) U |= g_[i].nimask;
+    U &= ~low_;
+    if (U_out) *U_out = U;
+    const int slots = L_ - jlow_;
+    return std::max(1, (std::popcount(U) + slots - 1) / slots);
+  }
+
+  // A staging of `rest` in at most `limit - depth` more stages, appended to
+  // cur_; remembers for each remaining set the allowance already proven
+  // too small.
+  bool shorter(const std::vector<int32_t>& rest, int depth, int limit) {
+    if (rest.empty()) return true;
+    if (out_) return false;
+    const int allow = limit - depth;
+    if (more_stages(rest, nullptr) > allow) return false;
+    const Key k = key_of(rest, 0);
+    auto it = too_few_.find(k);
+    if (it != too_few_.end() && it->second >= allow) return false;
+    if (!spend(kNodeCharge + (uint64_t)rest.size() * nsets())) return false;
+    const auto ch = stage_choices(g_, rest, n_, L_, jlow_, low_, all_);
+    std::unordered_map<Key, bool, KeyHash> tried;  // children with the same gates left
+    for (const auto& [taken, S] : ch) {
+      if (taken == 0 || out_) break;
+      std::vector<int32_t> left;
+      left.reserve(rest.size() - taken);
+      if (!spend(rest.size())) return false;
+      admitted(g_, rest, S, all_, nullptr, &left);
+      if (!tried.emplace(key_of(left, 0), true).second) continue;
+      cur_.push_back(S);
+      if (shorter(left, depth + 1, limit)) return true;
+      cur_.pop_back();
+    }
+    if (!out_) {
+      int& v = too_few_[k];
+      v = std::max(v, allow);
+    }
+    return false;
+  }
+
   bool spend(uint64_t w) {
     budget_ -= (int64_t)w;
     if (budget_ < 0) out_ = true;
@@ -269,10 +328,8 @@ class ExactStager {
       return;
     }
     uint64_t U = 0;
-    for (int32_t i : rest) U |= g_[i].nimask;
-    U &= ~low_;
+    const int more = more_stages(rest, &U);
     const int slots = L_ - jlow_;
-    const int more = std::max(1, (std::popcount(U) + slots - 1) / slots);
     const int lb_cost = depth == 0 ? std::max(0, std::popcount(U) - slots) : cost + std::popcount(U & ~last);
     if (depth + more > best_s_ || (depth + more == best_s_ && lb_cost >= best_cost_)) return;
     const Key k = key_of(rest, last);
@@ -309,14 +366,15 @@ class ExactStager {
   std::vector<uint64_t> best_, cur_;
   int best_s_ = 0, best_cost_ = 0;
   std::unordered_map<Key, std::pair<int, int>, KeyHash> seen_;
+  std::unordered_map<Key, int, KeyHash> too_few_;  // remaining gates -> stages proven too few
 };
 
 }  // namespace
 
 int stage_circuit(const std::vector<Gate>& g, int n, int L, int stager, int64_t budget, std::vector<Stage>* out,
-                  bool* optimal) {
+                  int* optimal) {
   out->clear();
-  *optimal = false;
+  *optimal = 0;
   if (L < 2 || L > n) return QS_EINVAL;
   const int jlow = std::max(0, L - kStageSlots);
   const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;

@@ -71,7 +71,7 @@ def test_exact_stager_plan_matches_oracle():
     g = C.mixed_circuit(n, 120, 3)
     plan = Q.Plan(n, g, local_qubits=L, shm_max_active=12, stager=Q.QS_STAGER_EXACT)
     st = plan.stats()
-    assert st.staging_optimal == 1 and st.num_stages > 1 and plan.validate() == 0
+    assert st.staging_optimal >= 1 and st.num_stages > 1 and plan.validate() == 0
     psi0 = random_state(n, 17)
     got = run_host(plan, n, psi0, nbuf=2)
     assert_close_state(got, sim.apply(n, g, psi0.copy()))
