@@ -71,8 +71,7 @@ struct State {
   std::vector<OpenK> ks;  // sorted canonically
   double closed = 0;
   double open_cost = 0;
-  int32_t hist = -1;
-  std::vector<Event> pend;  // this step's events, materialised if the state survives
+  int32_t hist = -1;  // last event of this state's history (Ctx::ev)
   double total() const { return closed + open_cost; }
 };
 
@@ -118,31 +117,45 @@ inline uint64_t conflict(uint64_t q1, uint64_t, uint64_t q2, uint64_t) { return 
 // kernels while the merged kernel is cheaper than the two.  Only kernels
 // whose ExtQ is "all qubits" are merged.
 // Returns the packed open cost and appends merge events when `rec` is set.
-double pack(Ctx& c, std::vector<OpenK> ks, bool rec, int32_t* hist) {
-  bool again = true;
-  while (again) {
-    again = false;
-    for (size_t i = 0; i < ks.size() && !again; ++i)
-      for (size_t j = i + 1; j < ks.size() && !again; ++j) {
-        OpenK& a = ks[i];
-        OpenK& b = ks[j];
-        if (a.fusion != b.fusion) continue;
-        // two all-extensible kernels commute with every gate after their
-        // first gates, so their union can sit after both sets of
-        // predecessors; any other pair could close a dependency cycle
-        if (a.ext != ALLQ || b.ext != ALLQ) continue;
-        OpenK m = a;
-        m.q |= b.q;
-        m.ni |= b.ni;
-        m.st.merge(b.st);
-        if (!c.fits(m)) continue;
-        if (c.kcost(m) >= c.kcost(a) + c.kcost(b)) continue;
-        if (rec) *hist = c.push(1, b.id, a.id, *hist);
-        a = m;
-        ks.erase(ks.begin() + j);
-        again = true;
-      }
+// The first merge the scan below takes, if any.
+bool first_merge(const Ctx& c, const std::vector<OpenK>& ks, size_t* ia, size_t* ib, OpenK* out) {
+  for (size_t i = 0; i < ks.size(); ++i)
+    for (size_t j = i + 1; j < ks.size(); ++j) {
+      const OpenK& a = ks[i];
+      const OpenK& b = ks[j];
+      if (a.fusion != b.fusion) continue;
+      // two all-extensible kernels commute with every gate after their
+      // first gates, so their union can sit after both sets of
+      // predecessors; any other pair could close a dependency cycle
+      if (a.ext != ALLQ || b.ext != ALLQ) continue;
+      OpenK m = a;
+      m.q |= b.q;
+      m.ni |= b.ni;
+      m.st.merge(b.st);
+      if (!c.fits(m)) continue;
+      if (c.kcost(m) >= c.kcost(a) + c.kcost(b)) continue;
+      *ia = i;
+      *ib = j;
+      *out = m;
+      return true;
+    }
+  return false;
+}
+
+double pack(Ctx& c, const std::vector<OpenK>& ks0, bool rec, int32_t* hist) {
+  size_t i = 0, j = 0;
+  OpenK m;
+  if (!first_merge(c, ks0, &i, &j, &m)) {  // nothing to merge: no copy
+    double s = 0;
+    for (const auto& k : ks0) s += c.kcost(k);
+    return s;
   }
+  std::vector<OpenK> ks = ks0;
+  do {
+    if (rec) *hist = c.push(1, ks[j].id, ks[i].id, *hist);
+    ks[i] = m;
+    ks.erase(ks.begin() + j);
+  } while (first_merge(c, ks, &i, &j, &m));
   double s = 0;
   for (const auto& k : ks) s += c.kcost(k);
   return s;
@@ -283,25 +296,33 @@ int plan_kernelize(PlanImpl* p) {
       for (size_t s = 0; s < std::max<size_t>(1, T / 2); ++s) keep.push_back(std::move(cur[r[s].second]));
       cur.swap(keep);
     }
-    std::unordered_map<uint64_t, std::vector<size_t>> index;
+    // successors by open-kernel set: hash -> the last state with that hash,
+    // chained through `chain` to the earlier ones
+    std::unordered_map<uint64_t, size_t> index;
+    std::vector<size_t> chain;
     std::vector<State> next, staged;
+    constexpr size_t kNone = ~size_t(0);
     auto offer = [&](State&& s) {
       std::sort(s.ks.begin(), s.ks.end());
-      uint64_t h = hash_state(s.ks);
-      auto& bucket = index[h];
-      for (size_t at : bucket)
+      const uint64_t h = hash_state(s.ks);
+      const auto it = index.try_emplace(h, kNone).first;
+      for (size_t at = it->second; at != kNone; at = chain[at])
         if (same_kernels(next[at].ks, s.ks)) {
           if (s.total() < next[at].total()) next[at] = std::move(s);
           return;
         }
-      bucket.push_back(next.size());
+      chain.push_back(it->second);
+      it->second = next.size();
       next.push_back(std::move(s));
     };
 
+    // buffers reused across states and candidates
+    std::vector<int> cands, restrict_now;
+    std::vector<State> branch, out;
     for (const State& st : cur) {
       // candidate placements: index of the kernel receiving u, or -1/-2 for a
       // new shared-memory / fusion singleton
-      std::vector<int> cands;
+      cands.clear();
       int sub = -1;
       for (size_t k = 0; k < st.ks.size(); ++k) {
         const OpenK& K = st.ks[k];
@@ -341,10 +362,10 @@ int plan_kernelize(PlanImpl* p) {
           ns.ks.push_back(K);
           tgt = (int)ns.ks.size() - 1;
         }
-        ns.pend.push_back(Event{0, (int32_t)ui, ns.ks[tgt].id, -1});
+        ns.hist = c.push(0, (int32_t)ui, ns.ks[tgt].id, ns.hist);
         // Alg. 4 for every other kernel; kernels about to lose "all qubits"
         // may merge with another all-extensible kernel instead (deferral).
-        std::vector<int> restrict_now;
+        restrict_now.clear();
         for (size_t k = 0; k < ns.ks.size(); ++k) {
           if ((int)k == tgt) continue;
           OpenK& K = ns.ks[k];
@@ -355,9 +376,10 @@ int plan_kernelize(PlanImpl* p) {
           }
         }
         // expand the merge choices kernel by kernel
-        std::vector<State> branch{std::move(ns)};
+        branch.clear();
+        branch.push_back(std::move(ns));
         for (int rk : restrict_now) {
-          std::vector<State> out;
+          out.clear();
           for (State& b : branch) {
             // option 1: restrict
             {
@@ -382,7 +404,7 @@ int plan_kernelize(PlanImpl* p) {
               m.st.merge(A.st);
               if (!c.fits(m)) continue;
               State r = b;
-              r.pend.push_back(Event{1, A.id, B.id, -1});
+              r.hist = c.push(1, A.id, B.id, r.hist);
               if ((int)o != tgt && !conflict(u.st.q, u.st.ni, B.q, B.ni)) {
                 // the merged kernel is restricted by u through A's qubits
                 m.ext = m.q & ~u.st.q;
@@ -410,25 +432,27 @@ int plan_kernelize(PlanImpl* p) {
         for (const OpenK& K : b.ks) want.push_back({K.st, K.fusion != 0});
       c.cm.prefetch(want);
     }
+    index.reserve(staged.size());
+    chain.reserve(staged.size());
+    next.reserve(staged.size());
     for (State& b : staged) {
       double open = 0;
-      std::vector<OpenK> keep;
-      for (const OpenK& K : b.ks) {
-        if (K.ext == 0) b.closed += c.kcost(K);
-        else {
-          keep.push_back(K);
+      size_t w = 0;  // kernels still open, compacted in place
+      for (size_t r = 0; r < b.ks.size(); ++r) {
+        const OpenK& K = b.ks[r];
+        if (K.ext == 0) {
+          b.closed += c.kcost(K);
+        } else {
           open += c.kcost(K);
+          if (w != r) b.ks[w] = K;
+          ++w;
         }
       }
-      b.ks.swap(keep);
+      b.ks.resize(w);
       b.open_cost = open;
       offer(std::move(b));
     }
     if (next.empty()) return QS_EPLAN;  // no feasible kernel for this gate
-    for (State& s2 : next) {
-      for (const Event& e : s2.pend) s2.hist = c.push(e.kind, e.a, e.b, s2.hist);
-      s2.pend.clear();
-    }
     if (c.ev.size() > (size_t(1) << 22)) compact(c, next);
     cur.swap(next);
     max_states = std::max<uint64_t>(max_states, cur.size());
