@@ -50,7 +50,7 @@ struct OpenK {
   uint64_t q = 0, ni = 0;  // mirrors of st.q / st.ni for the hot comparisons
   uint64_t ext = ALLQ;
   KStat st;
-  double cost = 0;         // the kernel's cost as it stands
+  double cost = -1;        // the kernel's cost as it stands, once known (< 0: not yet)
   int32_t id = -1;
   bool operator<(const OpenK& o) const {
     if (fusion != o.fusion) return fusion < o.fusion;
@@ -112,12 +112,9 @@ bool admits(const Ctx& c, const OpenK& k, const Unit& u) {
 // Alg. 4's intersection test: the gate shares a qubit with the kernel.
 inline uint64_t conflict(uint64_t q1, uint64_t, uint64_t q2, uint64_t) { return q1 & q2; }
 
-// Greedy packing of a state's open kernels (App. A.2 post-processing):
-// shared-memory kernels towards the largest feasible active set, fusion
-// kernels while the merged kernel is cheaper than the two.  Only kernels
-// whose ExtQ is "all qubits" are merged.
-// Returns the packed open cost and appends merge events when `rec` is set.
-// The first merge the scan below takes, if any.
+// The first pair of open kernels (in index order) that packing merges: both
+// of one type and all-extensible, the union feasible and cheaper than the
+// two.  Every kernel's cost must be known (OpenK::cost).
 bool first_merge(const Ctx& c, const std::vector<OpenK>& ks, size_t* ia, size_t* ib, OpenK* out) {
   for (size_t i = 0; i < ks.size(); ++i)
     for (size_t j = i + 1; j < ks.size(); ++j) {
@@ -133,7 +130,8 @@ bool first_merge(const Ctx& c, const std::vector<OpenK>& ks, size_t* ia, size_t*
       m.ni |= b.ni;
       m.st.merge(b.st);
       if (!c.fits(m)) continue;
-      if (c.kcost(m) >= c.kcost(a) + c.kcost(b)) continue;
+      m.cost = c.kcost(m);
+      if (m.cost >= a.cost + b.cost) continue;
       *ia = i;
       *ib = j;
       *out = m;
@@ -142,12 +140,17 @@ bool first_merge(const Ctx& c, const std::vector<OpenK>& ks, size_t* ia, size_t*
   return false;
 }
 
+// Greedy packing of a state's open kernels (App. A.2 post-processing):
+// shared-memory kernels towards the largest feasible active set, fusion
+// kernels while the merged kernel is cheaper than the two.  Only kernels
+// whose ExtQ is "all qubits" are merged.
+// Returns the packed open cost and appends merge events when `rec` is set.
 double pack(Ctx& c, const std::vector<OpenK>& ks0, bool rec, int32_t* hist) {
   size_t i = 0, j = 0;
   OpenK m;
   if (!first_merge(c, ks0, &i, &j, &m)) {  // nothing to merge: no copy
     double s = 0;
-    for (const auto& k : ks0) s += c.kcost(k);
+    for (const auto& k : ks0) s += k.cost;
     return s;
   }
   std::vector<OpenK> ks = ks0;
@@ -157,7 +160,7 @@ double pack(Ctx& c, const std::vector<OpenK>& ks0, bool rec, int32_t* hist) {
     ks.erase(ks.begin() + j);
   } while (first_merge(c, ks, &i, &j, &m));
   double s = 0;
-  for (const auto& k : ks) s += c.kcost(k);
+  for (const auto& k : ks) s += k.cost;
   return s;
 }
 
@@ -296,23 +299,27 @@ int plan_kernelize(PlanImpl* p) {
       for (size_t s = 0; s < std::max<size_t>(1, T / 2); ++s) keep.push_back(std::move(cur[r[s].second]));
       cur.swap(keep);
     }
-    // successors by open-kernel set: hash -> the last state with that hash,
-    // chained through `chain` to the earlier ones
-    std::unordered_map<uint64_t, size_t> index;
+    // successors by open-kernel set: an open-addressing table from the hash
+    // to the last state with that hash, chained through `chain` to the
+    // earlier ones
+    constexpr size_t kNone = ~size_t(0);
+    std::vector<std::pair<uint64_t, size_t>> table;
+    size_t tmask = 0;
     std::vector<size_t> chain;
     std::vector<State> next, staged;
-    constexpr size_t kNone = ~size_t(0);
     auto offer = [&](State&& s) {
       std::sort(s.ks.begin(), s.ks.end());
       const uint64_t h = hash_state(s.ks);
-      const auto it = index.try_emplace(h, kNone).first;
-      for (size_t at = it->second; at != kNone; at = chain[at])
+      size_t slot = (size_t)(h * 0x9E3779B97F4A7C15ull >> 20) & tmask;
+      while (table[slot].second != kNone && table[slot].first != h) slot = (slot + 1) & tmask;
+      auto& head = table[slot];
+      for (size_t at = head.second; at != kNone; at = chain[at])
         if (same_kernels(next[at].ks, s.ks)) {
           if (s.total() < next[at].total()) next[at] = std::move(s);
           return;
         }
-      chain.push_back(it->second);
-      it->second = next.size();
+      chain.push_back(head.second);
+      head = {h, next.size()};
       next.push_back(std::move(s));
     };
 
@@ -350,6 +357,7 @@ int plan_kernelize(PlanImpl* p) {
           K.q |= u.st.q;
           K.ni |= u.st.ni;
           K.st.merge(u.st);
+          K.cost = -1;
           tgt = cand;
         } else {
           OpenK K;
@@ -402,6 +410,7 @@ int plan_kernelize(PlanImpl* p) {
               m.q |= A.q;
               m.ni |= A.ni;
               m.st.merge(A.st);
+              m.cost = -1;
               if (!c.fits(m)) continue;
               State r = b;
               r.hist = c.push(1, A.id, B.id, r.hist);
@@ -429,21 +438,26 @@ int plan_kernelize(PlanImpl* p) {
     if (c.cm.learned) {
       std::vector<std::pair<KStat, bool>> want;
       for (const State& b : staged)
-        for (const OpenK& K : b.ks) want.push_back({K.st, K.fusion != 0});
+        for (const OpenK& K : b.ks)
+          if (K.cost < 0) want.push_back({K.st, K.fusion != 0});
       c.cm.prefetch(want);
     }
-    index.reserve(staged.size());
+    size_t tsize = 16;
+    while (tsize < 2 * staged.size()) tsize <<= 1;  // at most half full
+    table.assign(tsize, {0, kNone});
+    tmask = tsize - 1;
     chain.reserve(staged.size());
     next.reserve(staged.size());
     for (State& b : staged) {
       double open = 0;
       size_t w = 0;  // kernels still open, compacted in place
       for (size_t r = 0; r < b.ks.size(); ++r) {
-        const OpenK& K = b.ks[r];
+        OpenK& K = b.ks[r];
+        if (K.cost < 0) K.cost = c.kcost(K);  // kernels changed by this step
         if (K.ext == 0) {
-          b.closed += c.kcost(K);
+          b.closed += K.cost;
         } else {
-          open += c.kcost(K);
+          open += K.cost;
           if (w != r) b.ks[w] = K;
           ++w;
         }
