@@ -9,6 +9,7 @@
 // is a contiguous run in memory when the targets are high qubits) in shared
 // memory with U^T, and every thread accumulates a 4 x 4 block of outputs
 // in registers.
+#include <atomic>
 #include <algorithm>
 
 #include "internal.hpp"
@@ -148,11 +149,11 @@ int launch_fused(const FusedLaunch& a, cudaStream_t s) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  static unsigned attr_done = 0;
-  if (dev >= 32 || !((attr_done >> dev) & 1u)) {
+  static std::atomic<unsigned> attr_done{0};  // one bit per device ordinal < 32
+  if (dev >= 32 || !((attr_done.load() >> dev) & 1u)) {
     cudaFuncSetAttribute(fused_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float2) * ((1 << (2 * kMaxFuse)) + (1 << kTileLog))));
-    if (dev < 32) attr_done |= 1u << dev;
+    if (dev < 32) attr_done.fetch_or(1u << dev);
   }
   const uint64_t nb = 1ull << (a.n - a.k - P.cb);
   const int per_sm = std::max(1, (int)((200u << 10) / (smem + 2048)));

@@ -9,6 +9,7 @@
 // controls and diagonal factors on thread or batch bits use the known bit
 // value, and an exchange through a swizzled shared-memory tile changes the
 // register bits.  Finally the registers are stored back to HBM.
+#include <atomic>
 #include <algorithm>
 
 #include "internal.hpp"
@@ -460,19 +461,20 @@ __global__ void __launch_bounds__(1 << (M - kRegBits), 1 << (kMaxShmActive - M))
 
 template <int M>
 int launch_m(const V2Params& P, int n, cudaStream_t s) {
-  static int blocks_per_sm[64] = {0};
+  static std::atomic<int> blocks_per_sm[64];  // per device ordinal; 0: not yet set up
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = sizeof(float2) << M;
   const int threads = 1 << (M - kRegBits);
-  if (dev < 64 && blocks_per_sm[dev] == 0) {
+  int bps = dev < 64 ? blocks_per_sm[dev].load() : 0;
+  if (bps == 0) {
     cudaFuncSetAttribute(shm_kernel_v2<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, shm_kernel_v2<M>, threads, smem);
-    blocks_per_sm[dev] = std::max(1, b);
+    bps = std::max(1, b);
+    if (dev < 64) blocks_per_sm[dev].store(bps);
   }
-  const int bps = dev < 64 ? blocks_per_sm[dev] : 1;
   const uint64_t nb = 1ull << (n - M);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms * bps);
   shm_kernel_v2<M><<<(unsigned)grid, threads, smem, s>>>(P);

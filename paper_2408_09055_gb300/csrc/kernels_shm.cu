@@ -8,6 +8,7 @@
 // insular use the batch's known bit values: a control on a non-active qubit
 // enables or skips the gate for the whole batch; a diagonal factor on a
 // non-active qubit becomes a per-batch scalar.
+#include <atomic>
 #include <algorithm>
 
 #include "internal.hpp"
@@ -147,11 +148,11 @@ int launch_shm(const ShmLaunch& a, cudaStream_t s) {
   const size_t smem = sizeof(float2) << a.m;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
-  static unsigned attr_done = 0;  // one bit per device ordinal < 32
-  if (dev >= 32 || !((attr_done >> dev) & 1u)) {
+  static std::atomic<unsigned> attr_done{0};  // one bit per device ordinal < 32
+  if (dev >= 32 || !((attr_done.load() >> dev) & 1u)) {
     cudaFuncSetAttribute(shm_kernel_v1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(float2) << kMaxShmActive));
-    if (dev < 32) attr_done |= 1u << dev;
+    if (dev < 32) attr_done.fetch_or(1u << dev);
   }
   const uint64_t nb = 1ull << (a.n - a.m);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -19,6 +19,7 @@
 // whose waits are bounded in time (an expired wait sets an error flag, every
 // role leaves its loop, in-flight operations are waited for, tensor memory
 // is freed and the CTA returns).
+#include <atomic>
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -548,17 +549,17 @@ constexpr size_t tc_smem() {
 
 template <int CB, bool X3, int ST, bool WIDE, bool BULK = false, int RS = 1>
 int launch_tc(const TcParams& P, cudaStream_t s) {
-  static unsigned attr_done = 0;
+  static std::atomic<unsigned> attr_done{0};  // one bit per device ordinal < 32
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   constexpr size_t smem = tc_smem<CB, X3, ST, BULK, RS>();
   static_assert(smem <= 227u * 1024u - 2048u, "tensor-core pipeline exceeds shared memory");
-  if (dev >= 32 || !((attr_done >> dev) & 1u)) {
+  if (dev >= 32 || !((attr_done.load() >> dev) & 1u)) {
     cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
-    if (dev < 32) attr_done |= 1u << dev;
+    if (dev < 32) attr_done.fetch_or(1u << dev);
   }
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms);
