@@ -1,0 +1,52 @@
+"""Plans built from several threads at once (ctypes releases the GIL for the
+call) equal the plans built one at a time: the planner, the stager and the
+specialised-kernel compiler and its on-disk cache share no unguarded state."""
+import threading
+
+import pytest
+
+from synth import circuits as C
+
+Q = pytest.importorskip("paper_2408_09055_gb300.qsim")
+
+
+def _fingerprint(p):
+    out = []
+    for k in range(p.stats().num_kernels):
+        d = p.kernel(k)
+        out.append((d.type, d.qubit_mask, d.cost, tuple(p.kernel_gates(k))))
+    return out, [s["local_mask"] for s in p.stages()] if p.stats().num_stages > 1 else []
+
+
+CASES = [
+    (16, C.mixed_circuit(16, 300, 1), {}),
+    (16, C.entangling_circuit(16, 4, 2), {"fuse_kmax": 5}),
+    (18, C.mixed_circuit(18, 200, 3), {"local_qubits": 14, "stager": 1}),
+    (15, C.qft(15), {"shm_variant": 3}),
+]
+
+
+def test_concurrent_planning_is_deterministic(tmp_path, monkeypatch):
+    monkeypatch.setenv("QSIM_JIT_CACHE", str(tmp_path / "jit1"))
+    want = [_fingerprint(Q.Plan(n, g, shm_max_active=12, **kw)) for n, g, kw in CASES]
+    monkeypatch.setenv("QSIM_JIT_CACHE", str(tmp_path / "jit2"))  # cold: the threads fill it together
+    got, errors = {}, []
+
+    def work(t):
+        try:
+            for r in range(3):
+                i = (t + r) % len(CASES)
+                n, g, kw = CASES[i]
+                got[(t, r)] = (i, _fingerprint(Q.Plan(n, g, shm_max_active=12, **kw)))
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(t,)) for t in range(6)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    assert len(got) == 18
+    for i, fp in got.values():
+        assert fp == want[i]
