@@ -835,8 +835,8 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
   if (multi)
     for (auto& v : done) {
       v.assign(nch, nullptr);
-      for (auto& e : v)
-        if (rc == QS_OK) fail(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      for (auto& ev : v)
+        if (rc == QS_OK) fail(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
   uint64_t gchunk = 0;  // chunks take the buffers round-robin across stages
   for (size_t si = 0; si < plans.size() && rc == QS_OK; ++si) {
@@ -925,8 +925,8 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
     }
   }
   for (auto& v : done)
-    for (auto e : v)
-      if (e) cudaEventDestroy(e);
+    for (auto ev : v)
+      if (ev) cudaEventDestroy(ev);
   // join: the caller's stream continues after every chunk is back in host memory
   for (int b = 1; b < nbuf; ++b)
     if (ss[b] && evs[b] && cudaEventRecord(evs[b], ss[b]) == cudaSuccess) cudaStreamWaitEvent(ss[0], evs[b], 0);
