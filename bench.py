@@ -15,7 +15,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -221,7 +220,7 @@ def make_plan(Q, gates, which, shm_max=13, algo=None):
         return Q.Plan(N_QUBITS, gates, opts), f"{which}: Kernelize, every kernel a fused 2^6 unitary"
     if which == "B":  # learned-cost Kernelize, fused kernels on tensor cores in 3xTF32
         from paper_2408_09055_gb300 import costmodel as CM
-        net, meta = CM.load()
+        net, _ = CM.load()
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3,
                               shm_max_active=shm_max, fuse_kmax=6, mlp=net)
         if algo == "ordered":

@@ -24,10 +24,7 @@
 """
 from __future__ import annotations
 
-import itertools
-import math
-
-from synth.circuits import NQ, H, X, RX, RZ, U3, CX, CZ, CP, SWAP, RXX
+from synth.circuits import NQ, RZ, CX, CZ, CP
 
 INF = float("inf")
 

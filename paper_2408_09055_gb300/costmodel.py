@@ -49,13 +49,13 @@ def _sample_specs(n, count, seed, fused_fraction, precision, max_active=13):
         fused = rng.uniform() < fused_fraction
         gate_set = C.ALL_TYPES if i % 2 else C.MIXED_SET
         if fused:
-            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=6, gate_set=gate_set)
+            g, _ = C.random_subcircuit(n, seed=sub_seed, max_active=6, gate_set=gate_set)
             cost = Q.default_cost_table()
             for k in range(16):
                 cost.fuse_cost[k] = 1.0
             opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=6, precision=precision, cost=cost)
         else:
-            g, act = C.random_subcircuit(n, seed=sub_seed, max_active=max_active, gate_set=gate_set)
+            g, _ = C.random_subcircuit(n, seed=sub_seed, max_active=max_active, gate_set=gate_set)
             opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=0, shm_max_active=14)
         specs.append((g, opts, opts.cost))
     return specs
@@ -167,7 +167,7 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
     yr = np.zeros(0, dtype=np.float32)
     for r in range(rounds):
         specs = []
-        for c in range(circuits):
+        for _ in range(circuits):
             wseed = 20_000 + int(rng.integers(0, 1 << 30))
             ent = rng.uniform() < entangling_share
             g = C.entangling_circuit(n, 10, wseed) if ent else C.mixed_circuit(n, 1200, wseed)

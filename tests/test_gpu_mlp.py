@@ -139,5 +139,5 @@ def test_timing_generator_and_training_end_to_end():
     X, y, meta = CM.generate(n=18, count=48, seed=1, reps=2, batch=16, log=None)
     assert X.shape == (meta["count"], F) and meta["count"] >= 40
     assert np.all(np.isfinite(y))
-    net, metrics = CM.train(X, y, hidden=32, epochs=20, batch=16)
+    _, metrics = CM.train(X, y, hidden=32, epochs=20, batch=16)
     assert np.isfinite(metrics["train"]["mse"])

@@ -1,7 +1,6 @@
 """Pins of the FP64 MLP oracle: backprop against central finite differences,
 closed forms of the network and of Adam's first step."""
 import numpy as np
-import pytest
 
 from oracle import mlp
 

@@ -3,7 +3,6 @@ search and closed forms on tiny circuits, and the library's stager measured
 against it: the stager may not use fewer stages than the ILP's optimum (that
 would mean a broken ILP or a stage that breaks a dependency), and on these
 seeded circuits it reaches that optimum."""
-import numpy as np
 import pytest
 
 from oracle import plan as OP
@@ -57,7 +56,7 @@ def test_ilp_enforces_dependencies():
     # X(0), then CX(0 -> 1), then X(0): with L = 1 the middle gate needs
     # qubit 1 local, the others qubit 0, and no reordering is allowed
     g = C.make_gates([(C.X, 0), (C.CX, 0, 1), (C.X, 0)])
-    s, cost, stages = SI.stage(g, 2, 1)
+    s, _, stages = SI.stage(g, 2, 1)
     assert s == 3 and [ids for _, ids in stages] == [[0], [1], [2]]
 
 

@@ -108,7 +108,6 @@ def test_staged_plan_has_no_resident_form():
 
 def test_host_run_rejects_bad_arguments_before_device_work():
     # a misaligned or missing host state is refused before any CUDA call
-    import ctypes
     n = 14
     p = Q.Plan(n, C.mixed_circuit(n, 40, 3), local_qubits=12, shm_max_active=12, shm_variant=2)
     with pytest.raises(Q.QsError) as e:
