@@ -268,13 +268,42 @@ class ExactStager {
 
   // The lower bound on the stages still needed for `rest`: the non-insular
   // qubits it needs beyond the always-local ones, `slots` per stage.
-  int more_stages(const std::vector<int32_t>& rest, uint64_t* U_out) const {
+  //
+  // With `paths`, a second bound follows dependency paths: along a path of gates that
+  // each share a qubit with the next, stages never decrease, and the gates
+  // of one stage need at most `slots` free qubits together, so splitting the
+  // path greedily into runs that fit gives a number of stages no staging
+  // can beat.  One pass keeps a path per gate: the run count and the free
+  // qubits of its last run, extended from the last gate on each of its
+  // qubits (the most runs, then the fullest last run).
+  int more_stages(const std::vector<int32_t>& rest, uint64_t* U_out, bool paths) const {
     uint64_t U = 0;
     for (int32_t i : rest) U |= g_[i].nimask;
     U &= ~low_;
     if (U_out) *U_out = U;
     const int slots = L_ - jlow_;
-    return std::max(1, (std::popcount(U) + slots - 1) / slots);
+    int best = std::max(1, (std::popcount(U) + slots - 1) / slots);
+    if (!paths) return best;
+    struct Path {
+      int runs = 0;
+      uint64_t last = 0;  // free qubits of the last run
+    };
+    Path at_qubit[64];  // the path of the last gate seen on each qubit
+    for (int32_t i : rest) {
+      const Gate& x = g_[i];
+      const uint64_t need = x.nimask & ~low_;
+      Path p{1, need};
+      for (uint64_t m = x.qmask; m; m &= m - 1) {
+        const Path& a = at_qubit[std::countr_zero(m)];
+        if (a.runs == 0) continue;
+        const uint64_t u = a.last | need;
+        const Path c = std::popcount(u) > slots ? Path{a.runs + 1, need} : Path{a.runs, u};
+        if (c.runs > p.runs || (c.runs == p.runs && std::popcount(c.last) > std::popcount(p.last))) p = c;
+      }
+      for (uint64_t m = x.qmask; m; m &= m - 1) at_qubit[std::countr_zero(m)] = p;
+      best = std::max(best, p.runs);
+    }
+    return best;
   }
 
   // A staging of `rest` in at most `limit - depth` more stages, appended to
@@ -284,7 +313,8 @@ class ExactStager {
     if (rest.empty()) return true;
     if (out_) return false;
     const int allow = limit - depth;
-    if (more_stages(rest, nullptr) > allow) return false;
+    if (!spend(rest.size())) return false;  // the bounds' pass over the gates
+    if (more_stages(rest, nullptr, true) > allow) return false;
     const Key k = key_of(rest, 0);
     auto it = too_few_.find(k);
     if (it != too_few_.end() && it->second >= allow) return false;
@@ -328,7 +358,7 @@ class ExactStager {
       return;
     }
     uint64_t U = 0;
-    const int more = more_stages(rest, &U);
+    const int more = more_stages(rest, &U, false);  // the count is settled by phase 1
     const int slots = L_ - jlow_;
     const int lb_cost = depth == 0 ? std::max(0, std::popcount(U) - slots) : cost + std::popcount(U & ~last);
     if (depth + more > best_s_ || (depth + more == best_s_ && lb_cost >= best_cost_)) return;
