@@ -137,6 +137,23 @@ def test_plan_fused_matrix_matches_oracle():
     assert found > 0
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_plan_fused_matrices_are_unitary(precision):
+    # every fused kernel's FP64 product is unitary to 1e-12, widened kernels
+    # (six targets for the tensor-core precisions) included
+    n = 14
+    cost = Q.default_cost_table()
+    for k in range(16):
+        cost.fuse_cost[k] = 1.0
+    for g in (C.entangling_circuit(n, 3, 5), C.mixed_circuit(n, 200, 6), C.qft(n)):
+        plan = Q.Plan(n, g, algo=ORDERED, fuse_kmax=6, cost=cost, precision=precision, shm_variant=1)
+        for k in range(plan.stats().num_kernels):
+            if plan.kernel(k).type != Q.QS_KERNEL_FUSED:
+                continue
+            u = plan.fused_matrix(k)
+            assert np.max(np.abs(u @ u.conj().T - np.eye(len(u)))) <= 1e-12
+
+
 def test_invalid_inputs_are_rejected():
     g = C.make_gates([(C.CX, 0, 1)])
     with pytest.raises(Q.QsError):
