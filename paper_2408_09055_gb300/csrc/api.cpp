@@ -69,7 +69,8 @@ static int ensure_device(PlanImpl* p, DeviceCache** out) {
     if (!p->jit_modules[k].empty()) {
       e = cudaLibraryLoadData(&lib, p->jit_modules[k].data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
       if (e != cudaSuccess) {
-        for (auto l : dc.libs) cudaLibraryUnload(l);
+        for (auto l : dc.libs)
+          if (l) cudaLibraryUnload(l);
         return cuda_status(e);
       }
     }
@@ -97,10 +98,12 @@ static int ensure_device(PlanImpl* p, DeviceCache** out) {
   }
   if (host.empty()) host.resize(256);
   e = cudaMalloc(&dc.buf, host.size());
-  if (e != cudaSuccess) return cuda_status(e);
-  e = cudaMemcpy(dc.buf, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) dc.buf = nullptr;
+  else e = cudaMemcpy(dc.buf, host.data(), host.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    cudaFree(dc.buf);
+    if (dc.buf) cudaFree(dc.buf);
+    for (auto l : dc.libs)
+      if (l) cudaLibraryUnload(l);
     return cuda_status(e);
   }
   p->dev.push_back(std::move(dc));

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <deque>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -103,7 +104,7 @@ struct PlanImpl {
   LearnedCost* learned = nullptr;  // set while planning with QS_COST_LEARNED
   uint64_t dp_states = 0;
   std::mutex mu;
-  std::vector<DeviceCache> dev;     // one per device the plan ran on
+  std::deque<DeviceCache> dev;  // one per device the plan ran on; adding one moves no other
 };
 
 // ---- planner (planner.cpp) --------------------------------------------------
