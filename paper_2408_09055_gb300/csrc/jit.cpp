@@ -417,9 +417,15 @@ static void mkdirs(const std::string& d) {
 }
 
 static bool compile_one(const std::string& src, std::vector<char>* cubin, std::string* log) {
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+  // the cache name: two independent hashes of the source and the options,
+  // and the source length, so that no other program maps to the same file
+  std::string keyed = src;
+  for (const char* o : opts) (keyed += '\n') += o;
   const std::string dir = cache_dir();
-  char key[32];
-  std::snprintf(key, sizeof key, "%016" PRIx64, fnv1a(src));
+  char key[80];
+  std::snprintf(key, sizeof key, "%016" PRIx64 "%016zx-%zu", fnv1a(keyed), std::hash<std::string>{}(keyed),
+                src.size());
   const std::string path = dir + "/" + key + ".cubin";
   {
     std::ifstream f(path, std::ios::binary);
@@ -431,8 +437,7 @@ static bool compile_one(const std::string& src, std::vector<char>* cubin, std::s
   nvrtcProgram prog;
   if (nvrtcCreateProgram(&prog, src.c_str(), "qsim_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return false;
-  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
-  nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  nvrtcResult r = nvrtcCompileProgram(prog, (int)(sizeof opts / sizeof opts[0]), opts);
   if (r != NVRTC_SUCCESS) {
     size_t ls = 0;
     nvrtcGetProgramLogSize(prog, &ls);
