@@ -38,7 +38,19 @@ def test_status_strings_and_defaults_without_gpu():
     assert o.shm_max_active == 13 and o.forced_low == 4 and o.prune_T == 500 and o.algo == Q.QS_ALGO_KERNELIZE
 
 
-def test_binding_structs_match_the_header_layout(tmp_path):
+def test_binding_structs_match_the_header_layout():
+    import shutil
+    import tempfile
+    build = os.path.join(ROOT, "paper_2408_09055_gb300", "_build")
+    os.makedirs(build, exist_ok=True)
+    scratch = tempfile.mkdtemp(prefix="layout-", dir=build)
+    try:
+        _check_layout(scratch)
+    finally:
+        shutil.rmtree(scratch, ignore_errors=True)
+
+
+def _check_layout(scratch):
     # sizeof and every field offset of the header's structs, from a C
     # compiler, against the ctypes mirrors in the binding
     import shutil
@@ -55,11 +67,12 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         for f in S._fields_:
             lines.append(f'  printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
     lines += ["  return 0;", "}"]
-    src = tmp_path / "layout.c"
-    src.write_text("\n".join(lines) + "\n")
-    exe = tmp_path / "layout"
-    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+    src = os.path.join(scratch, "layout.c")
+    with open(src, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    exe = os.path.join(scratch, "layout")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([exe], check=True, capture_output=True,
                                                               text=True).stdout.splitlines())
     for S in structs:
         assert int(got[S.__name__]) == ctypes.sizeof(S), S.__name__

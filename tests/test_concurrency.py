@@ -1,6 +1,9 @@
 """Plans built from several threads at once (ctypes releases the GIL for the
 call) equal the plans built one at a time: the planner, the stager and the
 specialised-kernel compiler and its on-disk cache share no unguarded state."""
+import os
+import shutil
+import tempfile
 import threading
 
 import pytest
@@ -26,10 +29,21 @@ CASES = [
 ]
 
 
-def test_concurrent_planning_is_deterministic(tmp_path, monkeypatch):
-    monkeypatch.setenv("QSIM_JIT_CACHE", str(tmp_path / "jit1"))
+def test_concurrent_planning_is_deterministic(monkeypatch):
+    build = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2408_09055_gb300",
+                         "_build")
+    os.makedirs(build, exist_ok=True)
+    scratch = tempfile.mkdtemp(prefix="jit-concurrency-", dir=build)
+    try:
+        _run(scratch, monkeypatch)
+    finally:
+        shutil.rmtree(scratch, ignore_errors=True)
+
+
+def _run(scratch, monkeypatch):
+    monkeypatch.setenv("QSIM_JIT_CACHE", os.path.join(scratch, "jit1"))
     want = [_fingerprint(Q.Plan(n, g, shm_max_active=12, **kw)) for n, g, kw in CASES]
-    monkeypatch.setenv("QSIM_JIT_CACHE", str(tmp_path / "jit2"))  # cold: the threads fill it together
+    monkeypatch.setenv("QSIM_JIT_CACHE", os.path.join(scratch, "jit2"))  # cold: the threads fill it together
     got, errors = {}, []
 
     def work(t):
