@@ -943,11 +943,16 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
   return rc;
 }
 
-static int copy_amps(void* dst, const void* src, uint64_t first, uint64_t count, int n,
-                     cudaMemcpyKind kind, cudaStream_t s) {
+// Amplitudes [first, first + count) of a state, to or from host memory;
+// the range is checked before any address is formed.
+static int copy_amps(const qs_state* st, float* host, uint64_t first, uint64_t count, bool to_host,
+                     cudaStream_t s) {
   if (count == 0) return QS_OK;
-  if (first > (1ull << n) || count > (1ull << n) - first) return QS_EINVAL;
-  cudaError_t e = cudaMemcpyAsync(dst, src, count * sizeof(float2), kind, s);
+  const uint64_t size = 1ull << st->n;
+  if (first > size || count > size - first) return QS_EINVAL;
+  float2* dev = st->psi + first;
+  cudaError_t e = to_host ? cudaMemcpyAsync(host, dev, count * sizeof(float2), cudaMemcpyDeviceToHost, s)
+                          : cudaMemcpyAsync(dev, host, count * sizeof(float2), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return cuda_status(e);
 }
@@ -955,15 +960,13 @@ static int copy_amps(void* dst, const void* src, uint64_t first, uint64_t count,
 int qs_read_amplitudes(const qs_state* st, uint64_t first, uint64_t count, float* host_out,
                        void* stream) {
   if (!st || (!host_out && count)) return QS_EINVAL;
-  return copy_amps(host_out, st->psi + first, first, count, st->n, cudaMemcpyDeviceToHost,
-                   (cudaStream_t)stream);
+  return copy_amps(st, host_out, first, count, true, (cudaStream_t)stream);
 }
 
 int qs_write_amplitudes(qs_state* st, uint64_t first, uint64_t count, const float* host_in,
                         void* stream) {
   if (!st || (!host_in && count)) return QS_EINVAL;
-  return copy_amps(st->psi + first, host_in, first, count, st->n, cudaMemcpyHostToDevice,
-                   (cudaStream_t)stream);
+  return copy_amps(st, const_cast<float*>(host_in), first, count, false, (cudaStream_t)stream);
 }
 
 int qs_state_norm2(const qs_state* st, double* out, void* stream) {
