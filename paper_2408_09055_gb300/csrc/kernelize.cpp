@@ -116,14 +116,30 @@ inline uint64_t conflict(uint64_t q1, uint64_t, uint64_t q2, uint64_t) { return 
 // of one type and all-extensible, the union feasible and cheaper than the
 // two.  Every kernel's cost must be known (OpenK::cost).
 bool first_merge(const Ctx& c, const std::vector<OpenK>& ks, size_t* ia, size_t* ib, OpenK* out) {
-  for (size_t i = 0; i < ks.size(); ++i)
-    for (size_t j = i + 1; j < ks.size(); ++j) {
+  // two all-extensible kernels commute with every gate after their first
+  // gates, so their union can sit after both sets of predecessors; any other
+  // pair could close a dependency cycle.  Only those kernels are paired, in
+  // index order.
+  constexpr size_t kMaxListed = 256;
+  uint32_t all_ext[kMaxListed];
+  size_t na = 0, per_type[2] = {0, 0};
+  for (size_t i = 0; i < ks.size() && na < kMaxListed; ++i)
+    if (ks[i].ext == ALLQ) {
+      all_ext[na++] = (uint32_t)i;
+      per_type[ks[i].fusion ? 1 : 0]++;
+    }
+  if (na == kMaxListed) {  // too many to list: every all-extensible kernel, the slow way
+    na = 0;
+    per_type[0] = per_type[1] = 2;
+  }
+  if (per_type[0] < 2 && per_type[1] < 2) return false;
+  const size_t cnt = na ? na : ks.size();
+  for (size_t x = 0; x < cnt; ++x)
+    for (size_t y = x + 1; y < cnt; ++y) {
+      const size_t i = na ? all_ext[x] : x, j = na ? all_ext[y] : y;
       const OpenK& a = ks[i];
       const OpenK& b = ks[j];
       if (a.fusion != b.fusion) continue;
-      // two all-extensible kernels commute with every gate after their
-      // first gates, so their union can sit after both sets of
-      // predecessors; any other pair could close a dependency cycle
       if (a.ext != ALLQ || b.ext != ALLQ) continue;
       OpenK m = a;
       m.q |= b.q;
