@@ -232,14 +232,46 @@ std::vector<Unit> make_units(const PlanImpl* p, bool attach) {
         else if (owner[i] < 0) owner[i] = prev_multi;
       }
     }
+    // Gates on a qubit that no multi-qubit gate touches join the closest
+    // multi-qubit gate of the circuit (App. A.2), decided qubit by qubit:
+    // only when every unit they join still fits a kernel (the paper does not
+    // bound a unit's width); otherwise the qubit's gates stay together as a
+    // unit of their own, anchored at its first gate.  Nothing else touches
+    // such a qubit, so either way its gates keep their order and commute
+    // with the rest.
+    const uint64_t low = p->opts.forced_low <= 0 ? 0ull : ((1ull << std::min(p->opts.forced_low, p->n)) - 1);
+    auto fits_some_kernel = [&](const KStat& st) {
+      const uint64_t a = st.ni | low;
+      const bool shm = std::popcount(a) <= p->opts.shm_max_active && !(a & ~p->exec_limit);
+      const bool fused = p->opts.fuse_kmax > 0 && std::popcount(st.q) <= p->opts.fuse_kmax && !(st.q & ~p->exec_limit);
+      return shm || fused;
+    };
+    std::vector<KStat> ust(L);  // stats of the units formed so far, by anchor
     for (int i = 0; i < L; ++i)
-      if (owner[i] < 0) {
+      if (owner[i] >= 0) ust[owner[i]].add(p->gates[i], 0.0);
+    for (int q = 0; q < p->n; ++q) {
+      std::vector<int> lone;
+      for (int i = 0; i < L; ++i)
+        if (owner[i] < 0 && ((p->gates[i].qmask >> q) & 1)) lone.push_back(i);
+      if (lone.empty()) continue;
+      std::vector<int> to(lone.size());
+      std::vector<std::pair<int, KStat>> grown;  // anchor -> its stats with this qubit's gates
+      for (size_t t = 0; t < lone.size(); ++t) {
+        const int i = lone[t];
         auto it = std::lower_bound(multi.begin(), multi.end(), i);
         int best = -1;
         if (it != multi.end()) best = *it;
         if (it != multi.begin() && (best < 0 || i - *(it - 1) < best - i)) best = *(it - 1);
-        owner[i] = best;
+        to[t] = best;
+        auto g = std::find_if(grown.begin(), grown.end(), [&](const auto& e) { return e.first == best; });
+        if (g == grown.end()) g = grown.insert(grown.end(), {best, ust[best]});
+        g->second.add(p->gates[i], 0.0);
       }
+      const bool fits = std::all_of(grown.begin(), grown.end(), [&](const auto& e) { return fits_some_kernel(e.second); });
+      for (size_t t = 0; t < lone.size(); ++t) owner[lone[t]] = fits ? to[t] : lone[0];
+      if (fits)
+        for (const auto& e : grown) ust[e.first] = e.second;
+    }
   } else {
     for (int i = 0; i < L; ++i) owner[i] = i;
   }

@@ -106,6 +106,19 @@ def test_empty_circuit_is_identity():
     assert np.array_equal(got, ref.astype(np.complex64))
 
 
+def test_lone_qubit_gates_plan_and_run():
+    # Hadamards on qubits no multi-qubit gate touches form units of their own
+    # when attaching them would overfill a kernel
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n = 16
+    g = C.make_gates([(C.H, q) for q in range(n)] + [(C.CX, n - 1, 5), (C.CX, n - 2, 2), (C.H, 5)])
+    for variant in (1, 2, 3):
+        plan = Q.Plan(n, g, shm_max_active=12, fuse_kmax=0, shm_variant=variant)
+        got, _, _ = run_plan_on_gpu(n, plan)
+        assert_close_state(got, sim.apply(n, g))
+
+
 def test_closed_forms_on_gpu():
     need_gpu()
     from paper_2408_09055_gb300 import qsim as Q

@@ -162,3 +162,22 @@ def test_invalid_inputs_are_rejected():
         Q.Plan(4, g, shm_max_active=20)
     with pytest.raises(Q.QsError):
         Q.Plan(4, g, fuse_kmax=9)
+
+
+@pytest.mark.parametrize("n", [14, 20, 34])
+def test_lone_qubit_gates_do_not_overfill_a_unit(n):
+    # a Hadamard on every qubit, then CX gates on a few: the other qubits'
+    # Hadamards are only adjacent to single-qubit gates, so they attach to
+    # the closest multi-qubit gate (App. A.2) -- but not past what a kernel
+    # can hold; such a qubit's gates then form a unit of their own
+    g = C.make_gates([(C.H, q) for q in range(n)] + [(C.CX, n - 1, 5), (C.CX, n - 2, 2), (C.H, 5)])
+    for smax, kmax in ((12, 0), (10, 4), (14, 6)):
+        plan = Q.Plan(n, g, algo=KERNELIZE, shm_max_active=smax, fuse_kmax=kmax, shm_variant=1)
+        assert plan.validate() == 0
+        OP.check_plan(g, plan.kernels())
+    if n == 14:
+        from tests.program_emulator import run_plan
+        plan = Q.Plan(n, g, algo=KERNELIZE, shm_max_active=12, fuse_kmax=0, shm_variant=2)
+        got = run_plan(plan, n, sim.zero_state(n))
+        ref = sim.apply(n, g)
+        assert np.max(np.abs(got - ref)) <= 1e-5
