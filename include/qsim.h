@@ -112,7 +112,9 @@ typedef struct qs_plan_opts {
                              runs of complex64)                                */
   int32_t fuse_kmin;      /* fused kernels narrower than this are widened     */
   int32_t fuse_kmax;      /* widest fused kernel; 0 disables fusion            */
-  int32_t prune_T;        /* Kernelize pruning threshold T (<= 0: no pruning)  */
+  int32_t prune_T;        /* Kernelize pruning threshold T (<= 0: no pruning;
+                             a DP frontier above 2^20 states then makes
+                             qs_plan_circuit return QS_ENOMEM)              */
   int32_t attach_single;  /* Kernelize: attach one-qubit gates to neighbours   */
   int32_t local_qubits;   /* L: qubits resident on the GPU per chunk (0 or >= n:
                              no staging).  With 12 <= L < n the circuit is

@@ -39,6 +39,7 @@ namespace {
 
 constexpr double INF = std::numeric_limits<double>::infinity();
 constexpr uint64_t ALLQ = ~0ull;  // ExtQ = all qubits
+constexpr size_t kMaxDpStates = size_t(1) << 20;  // DP frontier limit (prune_T <= 0)
 
 struct Unit {
   std::vector<int32_t> gates;  // circuit indices in order
@@ -516,6 +517,9 @@ int plan_kernelize(PlanImpl* p) {
     }
     if (next.empty()) return QS_EPLAN;  // no feasible kernel for this gate
     if (c.ev.size() > (size_t(1) << 22)) compact(c, next);
+    // without pruning the frontier can grow exponentially (Theorem 5's
+    // bound): refuse before it takes the host's memory
+    if (next.size() > kMaxDpStates) return QS_ENOMEM;
     cur.swap(next);
     max_states = std::max<uint64_t>(max_states, cur.size());
   }

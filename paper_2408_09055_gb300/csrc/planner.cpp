@@ -89,12 +89,15 @@ static int plan_greedy(PlanImpl* p) {
   const bool fuse = p->opts.fuse_kmax > 0;
   const int lim = fuse ? p->opts.fuse_kmax : p->opts.shm_max_active;
   const uint64_t low = fuse ? 0 : low_mask(p->opts.forced_low, p->n);
+  // a kernel grows while it still fits: at most `lim` qubits, all of them
+  // ones a kernel may execute on (a stage's local positions)
+  auto fits = [&](uint64_t m) { return popc(m) <= lim && !(m & ~p->exec_limit); };
   Kernel cur;
   uint64_t cm = low;
   for (size_t i = 0; i < p->gates.size(); ++i) {
     const Gate& g = p->gates[i];
     uint64_t gm = fuse ? g.qmask : g.nimask;
-    if (!cur.gates.empty() && popc(cm | gm) > lim) {
+    if (!cur.gates.empty() && !fits(cm | gm)) {
       if (!finish_kernel(p, &cur)) return QS_EPLAN;
       p->kernels.push_back(std::move(cur));
       cur = Kernel();

@@ -5,7 +5,7 @@
 * OrderedKernelize (Alg. 5) reaches the brute-force optimum over all
   contiguous segmentations (Problem 1);
 * Kernelize (Alg. 3) without pruning or gate attachment costs no more than
-  OrderedKernelize (Theorem 5), and no less than the optimum over every
+  OrderedKernelize (Theorem 6), and no less than the optimum over every
   topologically equivalent order;
 * reported plan costs match the oracle's cost of the returned kernels.
 """

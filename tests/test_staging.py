@@ -125,3 +125,39 @@ def test_staged_empty_circuit():
     assert p.validate(C.make_gates([])) == 0
     assert p.stats().num_kernels == 0
     p.run_host(1 << 20)  # nothing to apply: returns before any device work
+
+
+def _sparse_circuit(rng, n, ng):
+    # all ten gate types, two-qubit gates only among a random subset of the
+    # qubits: regional insular qubits (CZ, CP partners, CX controls) and lone
+    # qubits both appear
+    from synth.circuits import NPARAM, NQ
+    pool = sorted(rng.choice(n, size=int(rng.integers(2, n)), replace=False).tolist())
+    items = []
+    for _ in range(ng):
+        t = int(rng.integers(0, 10))
+        th = list(rng.uniform(0, 6.28, size=NPARAM[t]))
+        if NQ[t] == 2:
+            a, b = rng.choice(pool, size=2, replace=False)
+            items.append((t, int(a), int(b), *th))
+        else:
+            items.append((t, int(rng.integers(0, n)), None, *th))
+    return C.make_gates(items)
+
+
+@pytest.mark.parametrize("algo", [1, 2, 3])
+def test_every_planner_stages_sparse_circuits(algo):
+    # each planner keeps its kernels on the stage's local positions, also
+    # when fused packing meets a regional insular qubit (the greedy packer
+    # once grew a fused kernel onto one and then fit no kernel type)
+    # (|A| <= 6 with four forced low qubits leaves two free active qubits:
+    # there a fused kernel on a regional qubit fits no shared-memory kernel)
+    rng = np.random.default_rng(7)
+    for it in range(40):
+        n = int(rng.integers(13, 17))
+        L = int(rng.integers(12, n))
+        g = _sparse_circuit(rng, n, int(rng.integers(20, 100)))
+        p = Q.Plan(n, g, algo=algo, local_qubits=L, shm_max_active=6, fuse_kmax=6 if it % 2 else 4,
+                   forced_low=4, shm_variant=1)
+        assert p.validate() == 0
+        OP.check_stages(g, stages_of(p), L)
