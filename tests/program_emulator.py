@@ -165,3 +165,56 @@ def run_plan(plan, n, psi):
         words, m, act, R = plan.kernel_program(k)
         run_kernel(psi, n, words, m, act, R)
     return psi
+
+
+def apply_unitary(psi, n, qubits, u):
+    """psi <- u on the given qubits (index bit j of u's rows and columns is
+    qubits[j]): gather, matrix product, scatter."""
+    k = len(qubits)
+    sub = np.zeros(1 << k, dtype=np.int64)
+    for j, q in enumerate(qubits):
+        sub |= ((np.arange(1 << k) >> j) & 1) << q
+    rest = [q for q in range(n) if q not in qubits]
+    base = np.zeros(1 << (n - k), dtype=np.int64)
+    for j, q in enumerate(rest):
+        base |= ((np.arange(1 << (n - k)) >> j) & 1) << q
+    idx = base[:, None] | sub[None, :]
+    psi[idx] = psi[idx] @ u.T
+
+
+def run_any_plan(plan, n, psi, fused_kernel_type=1):
+    """Applies any plan (fused kernels by their FP64 unitaries, shared-memory
+    kernels by their programs; a staged plan stage by stage on its chunk
+    view) to psi in place.  Returns None when a shared-memory kernel has no
+    register-phased program."""
+    L = plan.opts.local_qubits
+    stats = plan.stats()
+    if 0 < L < n:
+        idx = np.arange(1 << n)
+        views = []
+        for si in range(stats.num_stages):
+            st = plan.stage(si)
+            local = [q for q in range(n) if (st["local_mask"] >> q) & 1]
+            order = local + [q for q in range(n) if not (st["local_mask"] >> q) & 1]
+            logical = np.zeros_like(idx)
+            for p, q in enumerate(order):
+                logical |= ((idx >> p) & 1) << q
+            views.append((logical, {q: p for p, q in enumerate(order)},
+                          range(st["first_kernel"], st["first_kernel"] + st["num_kernels"])))
+    else:
+        views = [(None, {q: q for q in range(n)}, range(stats.num_kernels))]
+    for logical, pos, kernels in views:
+        view = psi if logical is None else psi[logical]
+        for k in kernels:
+            d = plan.kernel(k)
+            if d.type == fused_kernel_type:
+                apply_unitary(view, n, [pos[q] for q in range(n) if (d.qubit_mask >> q) & 1], plan.fused_matrix(k))
+            else:
+                try:
+                    words, m, act, R = plan.kernel_program(k)
+                except Exception:
+                    return None
+                run_kernel(view, n, words, m, act, R)
+        if logical is not None:
+            psi[logical] = view
+    return psi
