@@ -3,6 +3,7 @@ search and closed forms on tiny circuits, and the library's stager measured
 against it: the stager may not use fewer stages than the ILP's optimum (that
 would mean a broken ILP or a stage that breaks a dependency), and on these
 seeded circuits it reaches that optimum."""
+import numpy as np
 import pytest
 
 from oracle import plan as OP
@@ -127,3 +128,26 @@ def test_unknown_stager_is_rejected():
     with pytest.raises(Q.QsError) as e:
         Q.Plan(16, C.mixed_circuit(16, 50, 1), local_qubits=12, shm_max_active=12, stager=7)
     assert e.value.status == Q.QS_EINVAL
+
+
+def test_exact_stager_claims_on_random_sparse_circuits():
+    # whatever the exact stager claims proven must be the ILP's optimum; on
+    # these sparse circuits (all gate types, lone and regional insular
+    # qubits) it proves both the count and the objective
+    from tests.test_staging import _sparse_circuit
+    rng = np.random.default_rng(99)
+    proven = 0
+    for it in range(20):
+        n = int(rng.integers(13, 17))
+        L = int(rng.integers(12, n))
+        g = _sparse_circuit(rng, n, int(rng.integers(20, 120)))
+        p = Q.Plan(n, g, local_qubits=L, shm_max_active=12, fuse_kmax=0, shm_variant=1, stager=Q.QS_STAGER_EXACT)
+        st = p.stats()
+        s, cost, _ = SI.stage(g, n, L, fixed_local=range(max(0, L - 8)), s_max=16)
+        assert st.num_stages >= s
+        if st.staging_optimal >= 1:
+            assert st.num_stages == s
+        if st.staging_optimal == 2:
+            assert st.staging_cost == cost
+            proven += 1
+    assert proven >= 15
