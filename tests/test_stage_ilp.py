@@ -137,7 +137,7 @@ def test_exact_stager_claims_on_random_sparse_circuits():
     from tests.test_staging import _sparse_circuit
     rng = np.random.default_rng(99)
     proven = 0
-    for it in range(20):
+    for _ in range(20):
         n = int(rng.integers(13, 17))
         L = int(rng.integers(12, n))
         g = _sparse_circuit(rng, n, int(rng.integers(20, 120)))
