@@ -161,3 +161,18 @@ def test_every_planner_stages_sparse_circuits(algo):
                    forced_low=4, shm_variant=1)
         assert p.validate() == 0
         OP.check_stages(g, stages_of(p), L)
+
+
+@pytest.mark.parametrize("stager", [0, 1])
+def test_many_regional_qubits_use_the_grown_local_set(stager):
+    # with seven or more regional qubits the choices of local set exceed what
+    # the stager enumerates; it grows one in circuit order instead, and the
+    # exact search claims nothing
+    rng = np.random.default_rng(3)
+    for it in range(10):
+        n = int(rng.integers(19, 23))
+        L = int(rng.integers(12, n - 6))
+        g = _sparse_circuit(rng, n, int(rng.integers(20, 200))) if it % 2 else C.mixed_circuit(n, 300, it)
+        p = Q.Plan(n, g, local_qubits=L, shm_max_active=min(12, L), fuse_kmax=4, shm_variant=1, stager=stager)
+        assert p.validate() == 0 and p.stats().staging_optimal == 0
+        OP.check_stages(g, stages_of(p), L)
