@@ -127,7 +127,11 @@ typedef struct qs_plan_opts {
                              compiles, else interpreted, else generic),
                              1 generic tile kernel, 2 register-phased
                              interpreter, 3 register-phased kernel specialised
-                             per plan (NVRTC, sm_103a)                         */
+                             per plan (NVRTC, sm_103a).  2 and 3 make
+                             qs_plan_circuit return QS_EUNSUPPORTED when a
+                             kernel has no register-phased form (a tile below
+                             2^10, an active qubit above 31), 3 also when a
+                             kernel fails to compile                        */
   const qs_cost_table* cost; /* NULL: built-in table                           */
   const qs_mlp* mlp;         /* learned cost model (cost_kind = LEARNED)        */
   int64_t stager_budget;  /* QS_STAGER_EXACT: work limit in gate visits
@@ -147,7 +151,9 @@ typedef struct qs_plan qs_plan;
 /* Partition + Kernelize a circuit of `ngates` gates on `n` qubits (1..40).
  * The gate array is copied; the plan is owned by the caller and released
  * with qs_plan_free.  Errors: QS_EINVAL (bad gate, qubit or option),
- * QS_EPLAN (no feasible kernelization), QS_ENOMEM.                          */
+ * QS_EPLAN (a gate fits no kernel under the options' limits),
+ * QS_EUNSUPPORTED (tensor-core precisions with fusion below 11 qubits or
+ * above 6 targets; a forced shm_variant the plan cannot use), QS_ENOMEM.    */
 int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates,
                     const qs_plan_opts* opts, qs_plan** out);
 void qs_plan_free(qs_plan* plan);
