@@ -209,8 +209,9 @@ namespace {
 // set never hurts later stages, so that loses no staging.  Bounds at a
 // partial staging with remaining gates R, last local set P and d stages:
 // the non-insular qubits U of R outside the always-local ones need at least
-// ceil(|U| / free slots) more stages, and every qubit of U not in P must
-// still become local once.  A partial staging is also dropped when one with
+// ceil(|U| / free slots) more stages (and, while proving the count, as many
+// as some dependency path needs: more_stages), and every qubit of U not in P
+// must still become local once.  A partial staging is also dropped when one with
 // the same remaining gates and last set was reached with no more stages and
 // no more objective.
 class ExactStager {
@@ -269,8 +270,8 @@ class ExactStager {
   // The lower bound on the stages still needed for `rest`: the non-insular
   // qubits it needs beyond the always-local ones, `slots` per stage.
   //
-  // With `paths`, a second bound follows dependency paths: along a path of gates that
-  // each share a qubit with the next, stages never decrease, and the gates
+  // With `paths`, a second bound follows dependency paths: along a path of
+  // gates that each share a qubit with the next, stages never decrease, and the gates
   // of one stage need at most `slots` free qubits together, so splitting the
   // path greedily into runs that fit gives a number of stages no staging
   // can beat.  One pass keeps a path per gate: the run count and the free
