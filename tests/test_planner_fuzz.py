@@ -70,3 +70,25 @@ def test_random_circuits_and_options(seed):
         assert np.max(np.abs(got - ref)) <= 1e-5, (it, kw)
         checked += 1
     assert checked >= 15
+
+
+def test_planning_at_larger_sizes():
+    # 17 to 30 qubits, the benchmark families and random circuits, staged or
+    # not: every plan builds and is valid by the library and by the oracle
+    rng = np.random.default_rng(2024)
+    for it in range(12):
+        n = int(rng.integers(17, 31))
+        fam = it % 4
+        g = [lambda: C.mixed_circuit(n, int(rng.integers(100, 1500)), it),
+             lambda: C.entangling_circuit(n, int(rng.integers(1, 12)), it),
+             lambda: C.layered_u3_cz(n, int(rng.integers(1, 12)), it),
+             lambda: _circuit(rng, n)][fam]()
+        kw = dict(algo=int(rng.choice([1, 2, 3])), shm_max_active=int(rng.integers(8, 15)),
+                  fuse_kmax=int(rng.choice([0, 4, 6])), precision=int(rng.choice([0, 2])),
+                  forced_low=int(rng.choice([2, 4])), prune_T=int(rng.choice([16, 100])), shm_variant=1)
+        if it % 3 == 0:
+            kw["local_qubits"] = int(rng.integers(max(12, kw["shm_max_active"]), n))
+            kw["stager"] = int(rng.choice([0, 1]))
+        p = Q.Plan(n, g, **kw)
+        assert p.validate() == 0
+        OP.check_plan(g, p.kernels())
