@@ -170,3 +170,38 @@ def test_mixed_plans_reproduce_the_oracle(kind, precision, n, L):
     fid = abs(np.vdot(ref, psi)) ** 2 / (np.vdot(psi, psi).real * np.vdot(ref, ref).real)
     assert fid >= 1 - 1e-6, fid
     assert np.max(np.abs(psi - ref)) <= 1e-5
+
+
+def _stress_circuit(style, m, rng):
+    import itertools
+    items = []
+    if style == "allpairs":  # every pair of the active set, dense and diagonal
+        for a, b in itertools.combinations(range(m), 2):
+            items += [(C.CX, a, b), (C.U3, a, None, 0.3, 0.2, 0.1), (C.CP, b, a, 0.7)]
+    elif style == "swaps":  # register permutations across every phase
+        for _ in range(300):
+            a, b = rng.choice(m, size=2, replace=False)
+            items += [(C.SWAP, int(a), int(b)), (C.H, int(rng.integers(0, m)), None)]
+    else:  # the forced low qubits only: one long in-phase fusion run
+        for _ in range(300):
+            a, b = rng.choice(4, size=2, replace=False)
+            items.append((int(rng.choice([C.CX, C.CZ, C.RXX, C.SWAP])), int(a), int(b), 0.5))
+    return C.make_gates(items)
+
+
+@pytest.mark.parametrize("style", ["allpairs", "swaps", "lowonly"])
+@pytest.mark.parametrize("m", [10, 14])
+def test_programs_under_stress(style, m):
+    # long runs of two-qubit gates over a full active set stress the phase
+    # scheduler and the in-phase fusion; the emulated programs must still
+    # reproduce the oracle
+    from tests.program_emulator import run_any_plan
+    rng = np.random.default_rng(m)
+    n = m + 1
+    g = _stress_circuit(style, m, rng)
+    for algo in (2, 3):
+        p = Q.Plan(n, g, algo=algo, shm_max_active=m, fuse_kmax=0, shm_variant=2)
+        psi0 = _random_state(n, 7 * m + algo)
+        got = run_any_plan(p, n, psi0.copy())
+        assert got is not None
+        assert np.max(np.abs(got - sim.apply(n, g, psi0.copy()))) <= 1e-5
