@@ -38,6 +38,10 @@ extern "C" {
 const char* qs_strerror(int status);
 /* Text of the last CUDA error seen by this thread ("" if none). */
 const char* qs_last_cuda_error(void);
+/* Why this thread's last qs_plan_circuit call failed, e.g. the first gate
+ * that fits no kernel under the options' limits ("" after a success or when
+ * there is nothing to add to the status). */
+const char* qs_last_error(void);
 
 /* ---- circuit ------------------------------------------------------------
  * Gate set of the paper's benchmark workloads.  Matrices (the paper names

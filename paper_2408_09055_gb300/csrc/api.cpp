@@ -4,6 +4,7 @@
 #include <bit>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <new>
 
 #include "internal.hpp"
@@ -11,6 +12,7 @@
 namespace qs {
 
 static thread_local std::string g_last_cuda;
+static thread_local std::string g_last_error;  // why the last planning call failed
 
 void set_cuda_error(const char* what, cudaError_t e) {
   g_last_cuda = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
@@ -131,6 +133,7 @@ const char* qs_strerror(int s) {
 }
 
 const char* qs_last_cuda_error(void) { return g_last_cuda.c_str(); }
+const char* qs_last_error(void) { return g_last_error.c_str(); }
 
 void qs_cost_table_default(qs_cost_table* t) {
   if (!t) return;
@@ -276,8 +279,54 @@ static void free_device(PlanImpl& P) {
 
 extern "C" {
 
+static int plan_circuit_impl(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_plan_opts* opts,
+                             qs_plan** out);
+
+// Why planning failed, for the caller: the first gate that fits no kernel
+// on its own under the options' limits, else the limits that block a plan.
+static std::string plan_failure(int rc, int32_t n, const qs_gate* gates, uint64_t ngates, const qs_plan_opts& o) {
+  static const char* names[QS_NUM_GATE_TYPES] = {"H", "X", "RX", "RZ", "U3", "CX", "CZ", "CP", "SWAP", "RXX"};
+  char buf[256];
+  if (rc == QS_EPLAN) {
+    const uint64_t low = o.forced_low <= 0 ? 0ull : ((1ull << std::min(o.forced_low, (int)n)) - 1);
+    for (uint64_t i = 0; i < ngates; ++i) {
+      Gate g;
+      if (make_gate(gates[i], n, &g) != QS_OK) continue;
+      const int a = std::popcount(g.nimask | low), k = std::popcount(g.qmask);
+      if (a > o.shm_max_active && (o.fuse_kmax == 0 || k > o.fuse_kmax)) {
+        std::snprintf(buf, sizeof buf,
+                      "gate %llu (%s) fits no kernel: shared-memory needs %d active qubits > shm_max_active %d, "
+                      "fused needs %d > fuse_kmax %d",
+                      (unsigned long long)i, names[g.type], a, o.shm_max_active, k, o.fuse_kmax);
+        return buf;
+      }
+    }
+    return "no kernelization fits the options' limits (|A|, fused width, a stage's local qubits)";
+  }
+  if (rc == QS_EUNSUPPORTED) {
+    if (o.precision != QS_PREC_FP32 && o.fuse_kmax > 0 && (o.fuse_kmax > kTcTargets || n < kTcTargets + 5))
+      return "tensor-core precisions need n >= 11 and fuse_kmax <= 6";
+    if (o.shm_variant >= 2)
+      return "the forced shm_variant cannot serve every shared-memory kernel of this plan";
+  }
+  if (rc == QS_ENOMEM && o.prune_T <= 0) return "the unpruned Kernelize frontier passed 2^20 states";
+  return "";
+}
+
 int qs_plan_circuit(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_plan_opts* opts,
                     qs_plan** out) {
+  g_last_error.clear();
+  const int rc = plan_circuit_impl(n, gates, ngates, opts, out);
+  if (rc != QS_OK && rc != QS_EINVAL) {
+    qs_plan_opts o;
+    if (opts) o = *opts; else qs_plan_opts_default(&o);
+    g_last_error = plan_failure(rc, n, gates, ngates, o);
+  }
+  return rc;
+}
+
+static int plan_circuit_impl(int32_t n, const qs_gate* gates, uint64_t ngates, const qs_plan_opts* opts,
+                             qs_plan** out) {
   if (!out) return QS_EINVAL;
   *out = nullptr;
   if (n < 1 || n > kMaxQubits || (ngates > 0 && !gates)) return QS_EINVAL;

@@ -32,6 +32,9 @@ class QsError(RuntimeError):
         cuda = _lib.qs_last_cuda_error().decode()
         if status == QS_ECUDA and cuda:
             msg += f" [{cuda}]"
+        detail = _lib.qs_last_error().decode() if where == "qs_plan_circuit" else ""
+        if detail:
+            msg += f": {detail}"
         super().__init__(msg)
 
 
@@ -87,6 +90,7 @@ def _load():
     sigs = {
         "qs_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "qs_last_cuda_error": ([], ctypes.c_char_p),
+        "qs_last_error": ([], ctypes.c_char_p),
         "qs_plan_opts_default": ([ctypes.POINTER(qs_plan_opts)], None),
         "qs_cost_table_default": ([ctypes.POINTER(qs_cost_table)], None),
         "qs_plan_circuit": ([i32, vp, u64, ctypes.POINTER(qs_plan_opts), ctypes.POINTER(vp)], ctypes.c_int),

@@ -153,3 +153,19 @@ def test_network_handles_are_checked():
     assert L.qs_mlp_create(44, 16, 0, None) == EINVAL
     assert L.qs_mlp_forward(None, None, 1, None, 1, None) == EINVAL
     assert L.qs_mlp_gradient(None, None, None, 1, None, None, None) == EINVAL
+
+
+def test_planning_failures_say_why():
+    g = C.make_gates([(C.H, 0), (C.CX, 5, 6), (C.H, 2)])
+    with pytest.raises(Q.QsError) as e:
+        Q.Plan(8, g, shm_max_active=2, forced_low=2, fuse_kmax=0, shm_variant=1)
+    assert e.value.status == Q.QS_EPLAN
+    msg = L.qs_last_error().decode()
+    assert msg.startswith("gate 1 (CX) fits no kernel") and "3 active qubits > shm_max_active 2" in msg
+    assert "fits no kernel" in str(e.value)
+    with pytest.raises(Q.QsError) as e:
+        Q.Plan(8, g, precision=Q.QS_PREC_TF32X3, fuse_kmax=6)
+    assert e.value.status == EUNSUP and "n >= 11" in str(e.value)
+    # a success clears it
+    Q.Plan(8, g, shm_variant=1)
+    assert L.qs_last_error() == b""
