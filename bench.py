@@ -551,13 +551,21 @@ def main():
     st.read(out=hout, stream=sp)
     if world > 1:
         dist.barrier()
+    # events between the legs (the amplitude copies synchronise the stream):
+    # where the end-to-end time goes
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(e2e_steps)]
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for i in range(e2e_steps):
+        ev[i][0].record(stream)
         st.write(hin, stream=sp)
+        ev[i][1].record(stream)
         st.run(plan, sp)
+        ev[i][2].record(stream)
         st.read(out=hout, stream=sp)
+        ev[i][3].record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, "cuda")
+    legs = [sum(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(e2e_steps)) / e2e_steps for j in range(3)]
     e2e_norm = float(np.sum(np.abs(hout.astype(np.complex128)) ** 2))
 
     value = elapsed_ms / (args.steps * world)
@@ -584,6 +592,7 @@ def main():
         "e2e": {"value": e2e_ms / (e2e_steps * world) if world == 1 else e2e_ms / e2e_steps / world,
                 "unit": "ms/circuit", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(8 << n), "d2h_bytes_per_step": int(8 << n),
+                "breakdown_ms": {"h2d": legs[0], "circuit": legs[1], "d2h": legs[2]},
                 "norm2_out": e2e_norm},
     }
     del host_in, host_out
