@@ -64,3 +64,40 @@ def _run(scratch, monkeypatch):
     assert len(got) == 18
     for i, fp in got.values():
         assert fp == want[i]
+
+
+_FINGERPRINT = '''
+import hashlib, sys
+sys.path.insert(0, sys.argv[1])
+from synth import circuits as C
+from paper_2408_09055_gb300 import qsim as Q
+h = hashlib.sha256()
+for n, g, kw in ((24, C.mixed_circuit(24, 800, 5), {}), (18, C.mixed_circuit(18, 200, 2), {"local_qubits": 14, "stager": 1})):
+    p = Q.Plan(n, g, shm_max_active=12, shm_variant=1, **kw)
+    for k in range(p.stats().num_kernels):
+        d = p.kernel(k)
+        h.update(repr((d.type, d.qubit_mask, d.cost, list(p.kernel_gates(k)))).encode())
+    h.update(repr([s["local_mask"] for s in p.stages()]).encode())
+print(h.hexdigest())
+'''
+
+
+def test_plans_are_the_same_in_another_process():
+    # nothing in planning depends on addresses (which differ between
+    # processes): a fresh interpreter builds the same plans
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    runs = [subprocess.run([sys.executable, "-c", _FINGERPRINT, root], check=True, capture_output=True,
+                           text=True).stdout.strip() for _ in range(2)]
+    import contextlib
+    import io
+    here = io.StringIO()
+    saved = sys.argv
+    try:
+        sys.argv = ["fingerprint", root]
+        with contextlib.redirect_stdout(here):
+            exec(_FINGERPRINT, {"__name__": "fingerprint"})
+    finally:
+        sys.argv = saved
+    assert runs[0] == runs[1] == here.getvalue().strip() and len(runs[0]) == 64
