@@ -30,6 +30,10 @@ METRIC = "circuit time and HBM-roofline fraction at 30 qubits, FP32 vs fused 3xT
 N_QUBITS = 30
 N_GATES = 5000
 SEED = 100
+# DRAM bytes per launch of the specialised shared-memory kernel as a fraction
+# of its algorithmic bytes, from an ncu capture of that kernel form at 28
+# qubits (None: not measured for the current form)
+QSK_TRAFFIC_RATIO = None
 WORKLOAD = (f"mixed circuit, {N_QUBITS} qubits, {N_GATES} gates from {{H,X,RX,RZ,CX,CZ,CP,SWAP}}, "
             f"partner distance 1+Geom(0.3), seed {SEED}; complex64 state 8 GiB")
 
@@ -209,7 +213,7 @@ def reference_arm(args):
     return 0
 
 
-def make_plan(Q, gates, which, shm_max=13, algo=None):
+def make_plan(Q, gates, which, shm_max=13, algo=None, n=N_QUBITS, forced_low=4):
     if which.startswith("F-"):  # every kernel fused (k = 6), in the given precision
         prec = {"F-FP32": Q.QS_PREC_FP32, "F-TF32": Q.QS_PREC_TF32, "F-TF32X3": Q.QS_PREC_TF32X3}[which]
         cost = Q.default_cost_table()
@@ -217,38 +221,45 @@ def make_plan(Q, gates, which, shm_max=13, algo=None):
             cost.fuse_cost[k] = 1.0
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=prec, fuse_kmax=6, fuse_kmin=6,
                               cost=cost)
-        return Q.Plan(N_QUBITS, gates, opts), f"{which}: Kernelize, every kernel a fused 2^6 unitary"
+        return Q.Plan(n, gates, opts), f"{which}: Kernelize, every kernel a fused 2^6 unitary"
     if which == "B":  # learned-cost Kernelize, fused kernels on tensor cores in 3xTF32
         from paper_2408_09055_gb300 import costmodel as CM
         net, _ = CM.load()
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3,
-                              shm_max_active=shm_max, fuse_kmax=6, mlp=net)
+                              shm_max_active=shm_max, fuse_kmax=6, mlp=net, forced_low=forced_low)
         if algo == "ordered":
             opts.algo = Q.QS_ALGO_ORDERED
-        plan = Q.Plan(N_QUBITS, gates, opts)
+        plan = Q.Plan(n, gates, opts)
         plan._net = net  # the model must outlive planning only, kept for reference
         return plan, ("B: learned-cost Kernelize (MLP trained on this GPU's kernel timings), "
                       "shared-memory kernels + fused 3xTF32 tensor-core kernels")
     if which == "A" and algo == "ordered":
         opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, cost_kind=Q.QS_COST_ANALYTIC,
-                              precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0)
+                              precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0,
+                              forced_low=forced_low)
         label = "A': analytic-cost OrderedKernelize, shared-memory kernels, FP32"
     elif which == "A":
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, cost_kind=Q.QS_COST_ANALYTIC,
-                              precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0)
+                              precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0,
+                              forced_low=forced_low)
         label = "A: analytic-cost Kernelize, shared-memory kernels, FP32"
     else:
         raise ValueError(which)
-    return Q.Plan(N_QUBITS, gates, opts), label
+    return Q.Plan(n, gates, opts), label
 
 
-def workload_gates(name):
+def workload_gates(name, n=N_QUBITS):
     from synth import circuits as C
     if name == "mixed":
-        return C.mixed_circuit(N_QUBITS, N_GATES, SEED)
+        return C.mixed_circuit(n, N_GATES, SEED)
     if name == "entangling":
-        return C.entangling_circuit(N_QUBITS, 40, SEED)
+        return C.entangling_circuit(n, 40, SEED)
     raise ValueError(name)
+
+
+def entangling_desc(n):
+    return (f"entangling circuit, {n} qubits, 40 layers (U3 on every qubit, CP+RXX on a random "
+            f"matching, angles U[0,2pi)), seed {SEED}; complex64 state {8 << n >> 30} GiB")
 
 
 def profile_run(args):
@@ -426,6 +437,86 @@ def staged_measure(args):
     return 0
 
 
+def kernel_type_name(Q, plan, d):
+    ps = plan.stats()
+    if d.type == Q.QS_KERNEL_SHM:
+        return ("qsk<i> (plan-specialised shared-memory kernel)" if ps.num_jit else
+                "shm_kernel_v2" if ps.num_phased else "shm_kernel_v1")
+    return "fused_fp32_kernel" if plan.opts.precision == Q.QS_PREC_FP32 else "fused_tc_kernel"
+
+
+def by_kernel_type(Q, plan, per_kernel_ms, runs, n, hbm):
+    """Per kernel type: launches, total and average launch time (CUDA events
+    on the launching stream) and the HBM roofline fraction of one pass
+    (16 * 2^n bytes per launch) over the measured peak."""
+    out = {}
+    for k in range(plan.stats().num_kernels):
+        nm = kernel_type_name(Q, plan, plan.kernel(k))
+        t = out.setdefault(nm, {"launches": 0, "total_ms": 0.0})
+        t["launches"] += runs
+        t["total_ms"] += per_kernel_ms[k]
+    for t in out.values():
+        t["avg_launch_ms"] = t["total_ms"] / max(t["launches"], 1)
+        t["hbm_frac"] = 16.0 * (1 << n) / (t["avg_launch_ms"] * 1e-3) / 1e9 / hbm
+    return out
+
+
+def time_plan(Q, torch, st, plan, steps, warmup, stream, world):
+    """Warm-up runs, then `steps` timed runs of the plan on the resident
+    state, bracketed by synchronisation (and a barrier over ranks).  Returns
+    (max-over-ranks elapsed ms, per-kernel ms summed over runs, runs)."""
+    import torch.distributed as dist
+    sp = stream.cuda_stream
+    for _ in range(warmup):
+        st.run(plan, sp)
+    torch.cuda.synchronize()
+    timer = Q.Timer(plan, steps)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        st.run_timed(plan, timer, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    per_kernel_ms, runs = timer.read()
+    return elapsed, per_kernel_ms, runs
+
+
+def error_vs_fp64(Q, torch, shm_max, n=26):
+    """Each workload's plans A and B at n qubits against the FP64 oracle
+    (the same generators and seeds as the timed 30-qubit runs): fidelity
+    |<ref|psi>|^2 / (<ref|ref><psi|psi>) and max-abs error over every
+    amplitude, in FP64 on the host."""
+    import numpy as np
+    from oracle import sim
+    out = {"n_qubits": n, "reference": "FP64 (complex128) oracle, gate by gate"}
+    s = torch.cuda.current_stream().cuda_stream
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    st = Q.State(n, buf.data_ptr())
+    for wl in ("mixed", "entangling"):
+        g = workload_gates(wl, n)
+        t0 = time.perf_counter()
+        ref = sim.apply(n, g)
+        res = {"gates": int(len(g)), "oracle_s": time.perf_counter() - t0}
+        for which in ("A", "B"):
+            plan, _ = make_plan(Q, g, which, shm_max, None, n)
+            st.set_zero(s)
+            st.run(plan, s)
+            got = st.read(stream=s).astype(np.complex128)
+            fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
+            res[which] = {"fidelity": float(fid), "one_minus_fidelity": float(1.0 - fid),
+                          "max_abs": float(np.max(np.abs(ref - got))),
+                          "fused_kernels": int(plan.stats().num_fused)}
+            del got
+        out[wl] = res
+        del ref
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,7 +530,13 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="with --plan A, skip timing plan B beside it")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-entangling", action="store_true",
+                    help="with the default mixed workload, skip timing the entangling circuit's plans")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the 26-qubit error-against-FP64 leg (rank 0, beside the CPU baseline)")
     ap.add_argument("--shm-max", type=int, default=12)
+    ap.add_argument("--forced-low", type=int, default=4,
+                    help="lowest qubits forced into every shared-memory kernel (2^f * 8-byte runs)")
     ap.add_argument("--workload", default="mixed", choices=["mixed", "entangling"])
     ap.add_argument("--profile-run", type=int, default=0, metavar="N",
                     help="plan the workload's circuit generator at N qubits and run the plan "
@@ -477,66 +574,41 @@ def main():
     from synth import circuits as C
 
     gates = workload_gates(args.workload)
-    plan, label = make_plan(Q, gates, args.plan, args.shm_max, args.algo)
+    plan, label = make_plan(Q, gates, args.plan, args.shm_max, args.algo, forced_low=args.forced_low)
     ps = plan.stats()
-    kdesc = [plan.kernel(k) for k in range(ps.num_kernels)]
     n = N_QUBITS
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     st = Q.State(n, buf.data_ptr())
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     st.set_zero(sp)
-    for _ in range(args.warmup):
-        st.run(plan, sp)
-    torch.cuda.synchronize()
-    timer = Q.Timer(plan, args.steps)
+    hbm, _, src = peaks()
+    pass_bytes = 16.0 * (1 << n)
     clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        st.run_timed(plan, timer, sp)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    elapsed_ms, per_kernel_ms, runs = time_plan(Q, torch, st, plan, args.steps, args.warmup, stream, world)
     clk = clocks.stop()
-    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     if world > 1:
         dist.barrier()
-    per_kernel_ms, runs = timer.read()
     norm = st.norm2(sp)
 
     # roofline of the dominant kernel type (algorithmic bytes = one read and
     # one write of the state per launch)
-    pass_bytes = 16.0 * (1 << n)
-    by_type = {}
-    for k, d in enumerate(kdesc):
-        if d.type == Q.QS_KERNEL_SHM:
-            nm = ("qsk<i> (plan-specialised shared-memory kernel)" if ps.num_jit else
-                  "shm_kernel_v2" if ps.num_phased else "shm_kernel_v1")
-        else:
-            nm = "fused_fp32_kernel" if plan.opts.precision == Q.QS_PREC_FP32 else "fused_tc_kernel"
-        t = by_type.setdefault(nm, [0.0, 0])
-        t[0] += per_kernel_ms[k]
-        t[1] += runs
-    dom = max(by_type, key=lambda x: by_type[x][0])
-    avg_ms = by_type[dom][0] / max(by_type[dom][1], 1)
-    hbm, _, src = peaks()
+    types = by_kernel_type(Q, plan, per_kernel_ms, runs, n, hbm)
+    dom = max(types, key=lambda x: types[x]["total_ms"])
+    avg_ms = types[dom]["avg_launch_ms"]
     achieved = pass_bytes / (avg_ms * 1e-3) / 1e9
-    # DRAM bytes per launch: the ncu capture of the specialised kernel at 28
-    # qubits (profiles/qsk_shm_kernel_n28_full.md) moved 0.986 of the
-    # algorithmic bytes; scaled to this state (traffic grows with 2^n)
-    traffic = 0.986 * pass_bytes if dom.startswith("qsk") else None
+    # DRAM bytes per launch measured by ncu on the same specialised kernel
+    # form at 28 qubits (a 2 GiB state), as a fraction of its algorithmic
+    # bytes; DRAM traffic grows with the state, so the fraction carries over
+    traffic = QSK_TRAFFIC_RATIO * pass_bytes if (dom.startswith("qsk") and QSK_TRAFFIC_RATIO) else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic,
-            "traffic_source": ("ncu dram__bytes_read+write of the same kernel at 28 qubits, scaled x4"
-                               if traffic else None),
+            "traffic_source": ("ncu dram__bytes_read+write of the same kernel form at 28 qubits, "
+                               "as a fraction of its algorithmic bytes" if traffic else None),
             "peak_source": src,
-            "launches_timed": by_type[dom][1], "avg_launch_ms": avg_ms,
-            "share_of_step": by_type[dom][0] / max(sum(v[0] for v in by_type.values()), 1e-12)}
+            "launches_timed": types[dom]["launches"], "avg_launch_ms": avg_ms,
+            "share_of_step": types[dom]["total_ms"] / max(sum(v["total_ms"] for v in types.values()), 1e-12)}
 
     # end to end through the public API: H2D of the input state from pinned
     # memory, the circuit, D2H of the output state
@@ -567,26 +639,28 @@ def main():
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, "cuda")
     legs = [sum(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(e2e_steps)) / e2e_steps for j in range(3)]
     e2e_norm = float(np.sum(np.abs(hout.astype(np.complex128)) ** 2))
+    del host_in, host_out, hin, hout
 
     value = elapsed_ms / (args.steps * world)
+    launches = sum(v["launches"] for v in types.values())
     line = {
         "metric": METRIC, "value": value, "unit": "ms/circuit", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "mixed" else
-                   f"entangling circuit, {n} qubits, 40 layers (U3 on every qubit, CP+RXX on a random "
-                   f"matching), seed {SEED}",
+        "config": {"workload": WORKLOAD if args.workload == "mixed" else entangling_desc(n),
                    "n_qubits": n, "gates": int(len(gates)), "plan": label,
                    "kernels": int(ps.num_kernels), "shm_kernels": int(ps.num_shm),
                    "fused_kernels": int(ps.num_fused), "passes": int(ps.num_kernels),
                    "planner_ms": ps.planner_ms, "jit_ms": ps.jit_ms, "shm_max_active": args.shm_max,
+                   "forced_low": args.forced_low,
                    "model_cost_ms": ps.cost / 1e3, "l2": "no flush: the 8 GiB state exceeds L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gates_per_s": len(gates) / (value * 1e-3),
         "hbm_roofline_frac_circuit": ps.num_kernels * pass_bytes / (value * 1e-3) / 1e9 / hbm,
         "roofline": roof,
-        "gpu_launches": int(sum(v[1] for v in by_type.values())) * 1,
+        "kernel_types": types,
+        "gpu_launches": int(launches),
         "clocks": clk,
         "norm2_after": norm,
         "e2e": {"value": e2e_ms / (e2e_steps * world) if world == 1 else e2e_ms / e2e_steps / world,
@@ -595,44 +669,50 @@ def main():
                 "breakdown_ms": {"h2d": legs[0], "circuit": legs[1], "d2h": legs[2]},
                 "norm2_out": e2e_norm},
     }
-    del host_in, host_out
+
+    def arm(g, which, ref_ms=None):
+        """One more plan timed the same way on the same state."""
+        p, lab = make_plan(Q, g, which, args.shm_max, args.algo, forced_low=args.forced_low)
+        s_ = p.stats()
+        st.set_zero(sp)
+        ms, pk, r = time_plan(Q, torch, st, p, args.steps, args.warmup, stream, world)
+        v = ms / (args.steps * world)
+        out = {"plan": lab, "value": v, "unit": "ms/circuit",
+               "dtype": ("f32 shared-memory kernels, tf32x3 fused kernels"
+                         if p.opts.precision == Q.QS_PREC_TF32X3 else "f32"),
+               "kernels": int(s_.num_kernels), "shm_kernels": int(s_.num_shm),
+               "fused_kernels": int(s_.num_fused), "model_cost_ms": s_.cost / 1e3,
+               "planner_ms": s_.planner_ms, "jit_ms": s_.jit_ms,
+               "kernel_types": by_kernel_type(Q, p, pk, r, n, hbm),
+               "norm2_after": st.norm2(sp)}
+        if ref_ms is not None:
+            out["speedup_over_plan_a"] = ref_ms / v
+        return out, r * s_.num_kernels  # launches in its timed region
+
     if args.plan == "A" and not args.no_compare:
-        # the learned-cost plan with fused 3xTF32 kernels, timed the same way
-        # on the same state (the metric's second arm)
-        plan_b, label_b = make_plan(Q, gates, "B", args.shm_max, args.algo)
-        bs = plan_b.stats()
-        for _ in range(args.warmup):
-            st.run(plan_b, sp)
-        torch.cuda.synchronize()
-        tb = Q.Timer(plan_b, args.steps)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            st.run_timed(plan_b, tb, sp)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        b_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
-        pk, rb = tb.read()
-        kd = [plan_b.kernel(k) for k in range(bs.num_kernels)]
-        shm_ms = [pk[k] / rb for k in range(bs.num_kernels) if kd[k].type == Q.QS_KERNEL_SHM]
-        line["plan_b"] = {
-            "plan": label_b, "value": b_ms / (args.steps * world), "unit": "ms/circuit",
-            "dtype": "f32 shared-memory kernels, tf32x3 fused kernels",
-            "kernels": int(bs.num_kernels), "fused_kernels": int(bs.num_fused),
-            "model_cost_ms": bs.cost / 1e3, "planner_ms": bs.planner_ms,
-            "shm_avg_launch_ms": float(np.mean(shm_ms)) if shm_ms else None,
-            "shm_roofline_frac": (pass_bytes / (float(np.mean(shm_ms)) * 1e-3) / 1e9 / hbm) if shm_ms else None,
-            "norm2_after": st.norm2(sp),
-            "speedup_over_plan_a": (elapsed_ms / args.steps) / (b_ms / args.steps),
-        }
+        # the metric's second arm: the learned-cost plan with fused 3xTF32
+        # kernels, timed the same way on the same state
+        line["plan_b"], _ = arm(gates, "B", value)
+        if args.workload == "mixed" and not args.no_entangling:
+            # the dense entangling circuit (every layer U3 on every qubit and
+            # CP + RXX on a matching), where fused tensor-core kernels pay
+            eg = workload_gates("entangling")
+            ent = {"workload": entangling_desc(n), "gates": int(len(eg))}
+            ent["A"], _ = arm(eg, "A")
+            ent["B"], _ = arm(eg, "B", ent["A"]["value"])
+            line["entangling"] = ent
     if plan.opts.precision != Q.QS_PREC_FP32:
         line["dtype"] = {Q.QS_PREC_TF32: "tf32", Q.QS_PREC_TF32X3: "tf32x3"}[plan.opts.precision]
+    del st, buf
+    torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, thr = oracle_sample(gates, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "ms/circuit", "cores": thr, "kind": "oracle",
                                 "sample": desc}
+        if not args.no_error:
+            # error against FP64 of every timed plan, on the same generators
+            # at 26 qubits (the oracle cannot run 30 qubits in bench time)
+            line["error_vs_fp64"] = error_vs_fp64(Q, torch, args.shm_max)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

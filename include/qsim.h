@@ -252,8 +252,36 @@ int qs_state_set_zero(qs_state* st, void* stream); /* |0...0> */
 
 /* Applies the plan to the state, stream-ordered and asynchronous.  The first
  * call with a plan uploads its kernel programs (device allocation).  Errors
- * found asynchronously surface at the next synchronising call.             */
+ * found asynchronously surface at the next synchronising call: qs_sync,
+ * qs_read_amplitudes, qs_write_amplitudes, qs_state_norm2,
+ * qs_state_compare_c128, qs_apply_fused(_static).  A tensor-core kernel
+ * whose bounded wait (2 s) expired leaves its tiles unprocessed; that call
+ * then returns QS_ETIMEDOUT (once: the device's flag is cleared) and the
+ * state is undefined.                                                      */
 int qs_run_plan(const qs_plan* plan, qs_state* st, void* stream);
+
+/* Synchronises `stream` and reports errors of the work queued on it (and of
+ * earlier tensor-core work on this device): QS_ETIMEDOUT after an expired
+ * bounded wait, QS_ECUDA after a CUDA error, else QS_OK.                   */
+int qs_sync(void* stream);
+
+/* Test-only fault injection, no counterpart in the paper.  limit_us > 0:
+ * every later tensor-core launch (any process thread) first waits up to
+ * limit_us microseconds on an mbarrier that nothing ever signals, then gives
+ * up as an expired wait does -- every role leaves its loop, TMEM is freed
+ * and the CTA returns, with nothing issued to the tensor pipe -- so the
+ * launch leaves the state unchanged and the next synchronising call
+ * returns QS_ETIMEDOUT.  limit_us = 0 turns it off.  QS_EINVAL outside
+ * 0..10^7.                                                                  */
+int qs_debug_tc_stall(int64_t limit_us);
+
+/* Test-only, no counterpart in the paper: tensor-core fused launches made so
+ * far in this process, per load path: out[0] register gathers (32-bit
+ * offsets), out[1] bulk row copies (cp.async.bulk; chosen when a tile's 64
+ * columns are the 64 lowest qubits and five or more targets are at qubit
+ * 18 or above), out[2] register gathers with 64-bit offsets (n > 32).
+ * Writes min(cap, 3) entries; returns 3 (the number of paths) or QS_EINVAL. */
+int32_t qs_debug_tc_launch_counts(uint64_t* out, int32_t cap);
 
 /* Alg. 1's Execute with the state in host memory: for each stage, for each
  * chunk of 2^L amplitudes that share one value of the stage's regional
@@ -311,7 +339,8 @@ int qs_timer_read(qs_timer* timer, double* per_kernel_ms, uint64_t cap, uint64_t
 void qs_timer_free(qs_timer* timer);
 
 /* Copy amplitudes [first, first+count) between the state and host memory
- * (interleaved float pairs).  Synchronises the stream.                      */
+ * (interleaved float pairs).  Synchronises the stream; QS_ETIMEDOUT as for
+ * qs_sync.                                                                  */
 int qs_read_amplitudes(const qs_state* st, uint64_t first, uint64_t count,
                        float* host_out, void* stream);
 int qs_write_amplitudes(qs_state* st, uint64_t first, uint64_t count,
@@ -387,20 +416,25 @@ int qs_kernel_features(int32_t n, const qs_gate* gates, uint64_t ngates, int32_t
  * apply a gate -- code that runs with every byte of device memory already
  * handed to another allocator or budget, or that cannot accept the
  * synchronisation and failure modes of an allocation in the middle of its
- * work.  qs_apply_fused stages the 2^k x 2^k matrix in memory it allocates
- * on every call; this entry point stages it in one fixed device array
- * instead (128 KiB, held by every GPU that loads the library until the
- * process exits), so it calls no cudaMalloc, cudaFree or other allocating
+ * work.  qs_apply_fused stages what the kernel reads (the 2^k x 2^k matrix
+ * for FP32; the TF32 weights prepared from it, 64 or 128 KiB, for TF32 and
+ * 3xTF32) in memory it allocates on every call; this entry point stages it
+ * in one fixed device array instead (128 KiB, held by every GPU that loads
+ * the library until the process exits) and prepares the weights in static
+ * host memory, so it calls no cudaMalloc, cudaFree or other allocating
  * routine.
  *
- * Arguments, layout and results are those of qs_apply_fused.  Limit: k <= 7
- * (2^7 x 2^7 complex64 fills the array); a larger k returns QS_EINVAL.
+ * Arguments, layout and results are those of qs_apply_fused, for every
+ * precision: tensor-core precisions widen k < 6 to 6 and return
+ * QS_EUNSUPPORTED for k > 6 or n < 11.  Limit: k <= 7 (2^7 x 2^7 complex64
+ * fills the array); a larger k returns QS_EINVAL.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call on a device shares the array, which
- * keeps the last call's matrix; calls whose work overlaps on the GPU (for
- * example from two host threads on two streams) race on it and must be
- * serialised by the caller.  Synchronises the stream before returning.     */
+ * keeps the last call's contents (each call overwrites all it reads);
+ * calls whose work overlaps on the GPU (for example from two host threads
+ * on two streams) race on it and must be serialised by the caller.
+ * Synchronises the stream before returning; QS_ETIMEDOUT as for qs_sync.   */
 int qs_apply_fused_static(float* state_device, int32_t n, const int32_t* targets,
                           int32_t k, const float* u_host, int32_t precision, void* stream);
 

@@ -24,6 +24,31 @@ int cuda_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA;
 }
 
+void widen_unitary(const float* u, int k, int kw, float* out) {
+  const int dk = 1 << k, dw = 1 << kw;
+  for (int r = 0; r < dw; ++r)
+    for (int c = 0; c < dw; ++c) {
+      float re = 0.0f, im = 0.0f;
+      if ((r >> k) == (c >> k)) {
+        re = u[2 * ((r & (dk - 1)) * dk + (c & (dk - 1)))];
+        im = u[2 * ((r & (dk - 1)) * dk + (c & (dk - 1))) + 1];
+      }
+      out[2 * (r * dw + c)] = re;
+      out[2 * (r * dw + c) + 1] = im;
+    }
+}
+
+// targets[k .. kw-1] := the lowest qubits below n not among targets[0 .. k-1]
+void widen_targets(int n, int k, int kw, int* targets) {
+  uint64_t seen = 0;
+  for (int j = 0; j < k; ++j) seen |= 1ull << targets[j];
+  for (int q = 0, j = k; q < n && j < kw; ++q)
+    if (!((seen >> q) & 1)) {
+      targets[j++] = q;
+      seen |= 1ull << q;
+    }
+}
+
 // Uploads every kernel program of the plan to the current device (once per
 // device; later calls reuse it).
 static int ensure_device(PlanImpl* p, DeviceCache** out) {
@@ -66,6 +91,7 @@ static int ensure_device(PlanImpl* p, DeviceCache** out) {
   }
   // specialised kernels: load the JIT modules and look up each kernel
   dc.jit_kernel.assign(p->kernels.size(), nullptr);
+  dc.jit_blocks.assign(p->kernels.size(), 1);
   for (size_t k = 0; k < p->jit_modules.size(); ++k) {
     cudaLibrary_t lib = nullptr;
     if (!p->jit_modules[k].empty()) {
@@ -89,14 +115,20 @@ static int ensure_device(PlanImpl* p, DeviceCache** out) {
         if (l) cudaLibraryUnload(l);
       return cuda_status(e);
     }
-    const int smem = (int)(sizeof(float2) * pad_size(p->shm2[i].m));
+    const int smem = p->shm2[i].jit_smem;
     e = cudaKernelSetAttributeForDevice(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem, dev);
+    int blocks = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, (const void*)kf, 1 << (p->shm2[i].m - kRegBits),
+                                                         (size_t)smem);
+    if (e == cudaSuccess && blocks < 1) e = cudaErrorInvalidConfiguration;  // cannot be resident
     if (e != cudaSuccess) {
       for (auto l : dc.libs)
         if (l) cudaLibraryUnload(l);
       return cuda_status(e);
     }
     dc.jit_kernel[i] = kf;
+    dc.jit_blocks[i] = blocks;
   }
   if (host.empty()) host.resize(256);
   e = cudaMalloc(&dc.buf, host.size());
@@ -674,7 +706,7 @@ static int run_kernels(PlanImpl* P, DeviceCache* dc, float2* psi, int n_addr, ui
     }
     const uint8_t* base = static_cast<const uint8_t*>(dc->buf) + dc->op_off[i];
     if (K.type == QS_KERNEL_SHM && dc->jit_kernel[i]) {
-      rc = launch_jit(dc->jit_kernel[i], P->shm2[i], psi, n_addr, hi, s);
+      rc = launch_jit(dc->jit_kernel[i], P->shm2[i], dc->jit_blocks[i], psi, n_addr, hi, s);
     } else if (K.type == QS_KERNEL_SHM && P->shm2[i].ok) {
       ShmV2Launch a;
       a.psi = psi;
@@ -1003,7 +1035,8 @@ static int copy_amps(const qs_state* st, float* host, uint64_t first, uint64_t c
   cudaError_t e = to_host ? cudaMemcpyAsync(host, dev, count * sizeof(float2), cudaMemcpyDeviceToHost, s)
                           : cudaMemcpyAsync(dev, host, count * sizeof(float2), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return cuda_status(e);
+  if (e != cudaSuccess) return cuda_status(e);
+  return tc_check_error(s, true);
 }
 
 int qs_read_amplitudes(const qs_state* st, uint64_t first, uint64_t count, float* host_out,
@@ -1020,14 +1053,16 @@ int qs_write_amplitudes(qs_state* st, uint64_t first, uint64_t count, const floa
 
 int qs_state_norm2(const qs_state* st, double* out, void* stream) {
   if (!st || !out) return QS_EINVAL;
-  return launch_norm2(st->psi, st->n, out, (cudaStream_t)stream);
+  int rc = launch_norm2(st->psi, st->n, out, (cudaStream_t)stream);
+  return rc == QS_OK ? tc_check_error((cudaStream_t)stream, true) : rc;
 }
 
 int qs_state_compare_c128(const qs_state* st, const double* ref, double* fid, double* maxabs,
                           void* stream) {
   if (!st || !ref || !fid || !maxabs) return QS_EINVAL;
-  return launch_compare(st->psi, reinterpret_cast<const double2*>(ref), st->n, fid, maxabs,
-                        (cudaStream_t)stream);
+  int rc = launch_compare(st->psi, reinterpret_cast<const double2*>(ref), st->n, fid, maxabs,
+                          (cudaStream_t)stream);
+  return rc == QS_OK ? tc_check_error((cudaStream_t)stream, true) : rc;
 }
 
 int qs_remap(const float* in, float* out, int32_t n, const int32_t* perm, void* stream) {
@@ -1068,20 +1103,10 @@ int qs_apply_fused(float* state, int32_t n, const int32_t* targets, int32_t k, c
   } else {
     if (k > kTcTargets || n < kTcTargets + 5) return QS_EUNSUPPORTED;
     // widen to 6 targets with the lowest unused qubits: U (x) I
-    const int kw = kTcTargets, dk = 1 << k, dw = 1 << kw;
-    std::vector<float> uw(size_t(2) * dw * dw, 0.0f);
-    for (int r = 0; r < dw; ++r)
-      for (int c = 0; c < dw; ++c)
-        if ((r >> k) == (c >> k)) {
-          uw[2 * (r * dw + c)] = u_host[2 * ((r & (dk - 1)) * dk + (c & (dk - 1)))];
-          uw[2 * (r * dw + c) + 1] = u_host[2 * ((r & (dk - 1)) * dk + (c & (dk - 1))) + 1];
-        }
-    for (int q = 0, j = k; q < n && j < kw; ++q)
-      if (!((seen >> q) & 1)) {
-        a.targets[j++] = q;
-        seen |= 1ull << q;
-      }
-    a.k = kw;
+    std::vector<float> uw(size_t(2) << (2 * kTcTargets));
+    widen_unitary(u_host, k, kTcTargets, uw.data());
+    widen_targets(n, k, kTcTargets, a.targets);
+    a.k = kTcTargets;
     tc_prepare_weights(uw.data(), precision == QS_PREC_TF32X3, &staged);
   }
   const size_t bytes = staged.size() * sizeof(float);
@@ -1097,8 +1122,27 @@ int qs_apply_fused(float* state, int32_t n, const int32_t* targets, int32_t k, c
   int rc = launch_fused(a, s);
   cudaFreeAsync(du, s);
   if (rc == QS_OK) rc = cuda_status(cudaStreamSynchronize(s));
-  if (rc == QS_OK && precision != QS_PREC_FP32) rc = tc_check_error(true);
+  if (rc == QS_OK) rc = tc_check_error(s, true);
   return rc;
+}
+
+int qs_sync(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == QS_OK) rc = tc_check_error(s, true);
+  return rc;
+}
+
+int32_t qs_debug_tc_launch_counts(uint64_t* out, int32_t cap) {
+  if (!out || cap < 0) return QS_EINVAL;
+  tc_launch_counts(out, cap);
+  return kTcVariants;
+}
+
+int qs_debug_tc_stall(int64_t limit_us) {
+  if (limit_us < 0 || limit_us > 10000000) return QS_EINVAL;
+  tc_set_stall((uint64_t)limit_us * 1000ull);
+  return QS_OK;
 }
 
 }  // extern "C"

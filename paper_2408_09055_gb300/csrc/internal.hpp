@@ -38,6 +38,11 @@ int make_gate(const qs_gate& in, int n, Gate* out);
 bool gate_is_diagonal(int type);
 
 struct LearnedCost;  // learned.cpp
+// Discovery: between begin and end, a prediction not yet known reads as
+// infeasible and is recorded; end runs one batched inference of the recorded
+// kernels and returns whether there were any.
+void learned_collect_begin(LearnedCost* lc);
+bool learned_collect_end(LearnedCost* lc);
 
 // ---- plan ----------------------------------------------------------------
 struct Kernel {
@@ -83,6 +88,7 @@ struct DeviceCache {
   std::vector<uint64_t> prog_off;  // byte offset of kernel i's phased program
   std::vector<cudaLibrary_t> libs;     // loaded JIT modules
   std::vector<cudaKernel_t> jit_kernel;  // per plan kernel (nullptr: none)
+  std::vector<int> jit_blocks;           // its resident CTAs per SM
 };
 
 struct PlanImpl {
@@ -142,6 +148,19 @@ struct CostModel {
   double gate_cost(int type) const { return plan->cost.gate_cost[type]; }
   // batches the learned predictions of these kernels (no-op for analytic)
   void prefetch(const std::vector<std::pair<KStat, bool>>& ks) const;
+  // Runs f (which evaluates costs) with unknown learned predictions read as
+  // infeasible and recorded, then predicts the recorded ones in one batch;
+  // repeats until f needs nothing new (at most `rounds` times).  No-op for
+  // the analytic model.
+  template <class F>
+  void discover(F&& f, int rounds = 8) const {
+    if (!learned) return;
+    for (int r = 0; r < rounds; ++r) {
+      learned_collect_begin(learned);
+      f();
+      if (!learned_collect_end(learned)) break;
+    }
+  }
 };
 // learned.cpp
 LearnedCost* learned_create(const PlanImpl* p, qs_mlp* mlp, int* status);
@@ -208,7 +227,13 @@ bool compile_shm_v2(const PlanImpl* p, const Kernel& K, const ShmProgram& sp, Sh
 void fold_global_phase(std::vector<ShmProgramV2>& progs);
 int jit_compile_plan(PlanImpl* p);                 // jit.cpp
 bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::string* out);
-int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, uint64_t hi, cudaStream_t s);
+// batch-load form, dynamic shared memory (bytes) and launch-bound CTAs per SM
+// of a program's specialised kernel
+void jit_shape(const ShmProgramV2& pg, int* form, int* smem, int* min_blocks);
+// blocks_per_sm: resident CTAs of the kernel per SM (the grid is that many
+// per SM, so the grid-stride loop has no partial last wave)
+int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, int blocks_per_sm, float2* psi, int n, uint64_t hi,
+               cudaStream_t s);
 
 struct FusedLaunch {
   float2* psi;
@@ -219,8 +244,22 @@ struct FusedLaunch {
 };
 int launch_fused(const FusedLaunch& a, cudaStream_t s);
 constexpr int kTcTargets = 6;  // width of the tensor-core fused kernel
+constexpr size_t tc_weight_floats(bool x3) { return size_t(x3 ? 2 : 1) * 128 * 128; }
 void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out);
-int tc_check_error(bool clear);
+void tc_prepare_weights_into(const float* u, bool x3, float* out);  // tc_weight_floats(x3) floats
+// QS_ETIMEDOUT if a tensor-core kernel's bounded wait expired in work queued
+// on s before this call (synchronises s); clear resets the flag.
+int tc_check_error(cudaStream_t s, bool clear);
+void tc_set_stall(uint64_t ns);  // test-only fault injection (qs_debug_tc_stall)
+// tensor-core load paths: register gathers with 32-bit offsets, bulk row
+// copies (rows in many 2 MiB pages), register gathers with 64-bit offsets
+enum TcVariant { kTcRegister = 0, kTcBulk = 1, kTcWide = 2, kTcVariants = 3 };
+void tc_launch_counts(uint64_t* out, int cap);
+// U (2^k x 2^k, row-major complex64) widened to 2^kw x 2^kw as U (x) I on
+// kw - k added index bits above bit k-1; out: 2 * 4^kw floats.
+void widen_unitary(const float* u, int k, int kw, float* out);
+// targets[k .. kw-1] := the lowest qubits below n not in targets[0 .. k-1]
+void widen_targets(int n, int k, int kw, int* targets);
 
 int launch_set_zero(float2* psi, int n, cudaStream_t s);
 int launch_norm2(const float2* psi, int n, double* out_host, cudaStream_t s);

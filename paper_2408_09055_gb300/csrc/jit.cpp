@@ -92,6 +92,7 @@ struct Gen {
   std::ostringstream o;
   int nm[kRegAmps];  // register index j -> variable r<nm[j]>
   int phase = 0;
+  std::string after_last_xchg;  // emitted once the last exchange has read the tile
   explicit Gen(const ShmProgramV2& p) : pg(p) {
     for (int j = 0; j < kRegAmps; ++j) nm[j] = j;
   }
@@ -146,6 +147,7 @@ struct Gen {
       o << v(j) << "=tile[sp" << next_index << "+" << pad_index(li) << "u];\n";
     }
     phase = next_index;
+    if (next_index == (int)pg.maps.size() - 1) o << after_last_xchg;
   }
 
   bool body() {
@@ -334,9 +336,40 @@ std::string thread_expr(const PhaseMap& pm, const uint64_t* value_of_local) {
 
 }  // namespace
 
+// Batch-load form of a specialised kernel: QSIM_JIT_PREFETCH = 0, 1 or 2
+// overrides the default, 0.  Measured on the 30-qubit mixed circuit (|A| <=
+// 12): loads straight into registers 3.40 ms per launch; a cp.async prefetch
+// of the next batch into a separate staging buffer 4.27 ms (3 instead of 4
+// CTAs per SM); the prefetch into the exchange tile after the last exchange
+// 3.47 ms.
+static int prefetch_form() {
+  const char* e = std::getenv("QSIM_JIT_PREFETCH");
+  if (e && (e[0] == '0' || e[0] == '1' || e[0] == '2') && !e[1]) return e[0] - '0';
+  return 0;
+}
+
+void jit_shape(const ShmProgramV2& pg, int* form, int* smem, int* min_blocks) {
+  const int m = pg.m;
+  const bool xch = pg.maps.size() > 1;
+  const size_t tile = sizeof(float) * 2 * pad_size(m), stg = sizeof(float) * 2 << m;
+  const int f = prefetch_form();
+  size_t bytes;
+  if (f == 0) bytes = tile;                       // loads straight into registers
+  else if (f == 1) bytes = (xch ? tile : 0) + stg;  // staging beside the exchange tile
+  else bytes = xch ? tile : stg;                  // staging inside the exchange tile
+  // CTAs per SM: what shared memory allows (227 KiB, 1 KiB reserved per
+  // CTA), at most 2^(14-m) so that a thread keeps >= 128 registers
+  int mb = 1 << (kMaxShmActive - m);
+  if (f != 0) mb = std::max(1, std::min(mb, (int)((227u << 10) / (bytes + 1024))));
+  *form = f;
+  *smem = (int)bytes;
+  *min_blocks = mb;
+}
+
 bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::string* out) {
   const int m = pg.m;
   const int nt = m - kRegBits;
+  const unsigned nthr = 1u << nt;
   Gen g(pg);
   std::ostringstream& o = g.o;
   uint64_t phys[kMaxShmActive], padv[kMaxShmActive];
@@ -345,8 +378,26 @@ bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::str
     padv[j] = pad_index(1u << j);
     if (pg.act[j] >= 32) return false;
   }
-  const int minb = 1 << (kMaxShmActive - m);
-  o << "extern \"C\" __global__ void __launch_bounds__(" << (1 << nt) << ", " << minb << ")\n"
+  int form = 0, smem = 0, minb = 1;
+  jit_shape(pg, &form, &smem, &minb);
+  const bool xch = pg.maps.size() > 1;
+  uint64_t ld_off[kRegAmps];
+  {
+    const PhaseMap& lm = pg.maps.front();
+    for (int j = 0; j < kRegAmps; ++j) {
+      ld_off[j] = 0;
+      for (int i = 0; i < kRegBits; ++i)
+        if ((j >> i) & 1) ld_off[j] |= phys[lm.R[i]];
+    }
+  }
+  // the batch's base address: batch index bits spread over the non-active qubits
+  o << "static __device__ __forceinline__ unsigned long long " << name
+    << "_base(unsigned long long bt) {\nreturn 0ull";
+  for (int r = 0; r < pg.nruns; ++r)
+    o << " | (((bt >> " << (int)pg.run_src[r] << ") & " << ((1ull << pg.run_len[r]) - 1) << "ull) << "
+      << (int)pg.run_dst[r] << ")";
+  o << ";\n}\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << nthr << ", " << minb << ")\n"
     << name << "(float2* __restrict__ psi, unsigned long long nb, unsigned long long hi) {\n"
     << "extern __shared__ float2 tile[];\n"
     << "const unsigned tid = threadIdx.x;\n";
@@ -354,20 +405,40 @@ bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::str
   o << "const unsigned pts = " << thread_expr(pg.maps.back(), phys) << ";\n";
   for (size_t p = 0; p < pg.maps.size(); ++p)
     o << "const unsigned sp" << p << " = " << thread_expr(pg.maps[p], padv) << ";\n";
+  std::string issue;  // prefetch of batch bt + gridDim.x into this thread's staging slots
+  if (form != 0) {
+    // staging slot of register j of thread t: float2 index j * nthr + t
+    // (consecutive lanes, consecutive 8-byte words: no bank conflicts)
+    const uint32_t stg0 = (form == 1 && xch) ? pad_size(m) : 0;
+    o << "float2* const stg = tile + " << stg0 << "u;\n";
+    o << "unsigned ss;\nasm(\"{.reg .u64 t; cvta.to.shared.u64 t, %1; cvt.u32.u64 %0, t;}\" : \"=r\"(ss) : "
+         "\"l\"(stg + tid));\n";
+    std::ostringstream is;
+    is << "{\nconst unsigned long long nbt = bt + gridDim.x;\nif (nbt < nb) {\n"
+       << "unsigned long long gp;\nasm(\"cvta.to.global.u64 %0, %1;\" : \"=l\"(gp) : \"l\"(psi + (" << name
+       << "_base(nbt) | ptl)));\n";
+    for (int j = 0; j < kRegAmps; ++j)
+      is << "asm volatile(\"cp.async.ca.shared.global [%0+" << (8u * nthr * (uint32_t)j) << "], [%1+"
+         << (8ull * ld_off[j]) << "], 8;\" :: \"r\"(ss), \"l\"(gp) : \"memory\");\n";
+    is << "}\nasm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n}\n";
+    issue = is.str();
+    // the first batch: nothing else uses the staging slots yet
+    o << "{\nconst unsigned long long bt = (unsigned long long)blockIdx.x - gridDim.x;\n" << issue << "}\n";
+  }
   o << "for (unsigned long long bt = blockIdx.x; bt < nb; bt += gridDim.x) {\n";
-  o << "const unsigned long long base = 0ull";
-  for (int r = 0; r < pg.nruns; ++r)
-    o << " | (((bt >> " << (int)pg.run_src[r] << ") & " << ((1ull << pg.run_len[r]) - 1) << "ull) << "
-      << (int)pg.run_dst[r] << ")";
-  o << ";\n";
-  o << "const float2* __restrict__ ip = psi + (base | ptl);\n";
-  {
-    const PhaseMap& lm = pg.maps.front();
-    for (int j = 0; j < kRegAmps; ++j) {
-      uint64_t off = 0;
-      for (int i = 0; i < kRegBits; ++i)
-        if ((j >> i) & 1) off |= phys[lm.R[i]];
-      o << "float2 r" << j << " = ip[" << off << "u];\n";
+  o << "const unsigned long long base = " << name << "_base(bt);\n";
+  if (form == 0) {
+    o << "const float2* __restrict__ ip = psi + (base | ptl);\n";
+    for (int j = 0; j < kRegAmps; ++j) o << "float2 r" << j << " = ip[" << ld_off[j] << "u];\n";
+  } else {
+    o << "asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");\n";
+    for (int j = 0; j < kRegAmps; ++j) o << "float2 r" << j << " = stg[" << (nthr * (uint32_t)j) << "u + tid];\n";
+    if (form == 1 || !xch) {
+      o << issue;  // own slots only: read above, refilled now
+    } else {
+      // the exchange tile holds the slots: refill once every thread has read
+      // the last exchange's values
+      g.after_last_xchg = "__syncthreads();\n" + issue;
     }
   }
   if (!g.body()) return false;
@@ -482,7 +553,9 @@ int jit_compile_plan(PlanImpl* p) {
   std::vector<std::vector<int>> members;
   for (int i : idx) {
     std::string name = "qsk" + std::to_string(i), s;
-    if (!jit_source(p->shm2[i], p->n, name, &s)) continue;
+    ShmProgramV2& pg = p->shm2[i];
+    jit_shape(pg, &pg.jit_prefetch, &pg.jit_smem, &pg.jit_min_blocks);
+    if (!jit_source(pg, p->n, name, &s)) continue;
     if (srcs.empty() || srcs.back().size() + s.size() > budget) {
       srcs.emplace_back();
       members.emplace_back();

@@ -337,6 +337,13 @@ int plan_kernelize(PlanImpl* p) {
                 want.push_back({m, s.ks[i].fusion != 0});
               }
         c.cm.prefetch(want);
+        // merges of merged kernels: discovered and predicted in batches
+        c.cm.discover([&]() {
+          for (const State& st : cur) {
+            int32_t dummy = -1;
+            pack(c, st.ks, false, &dummy);
+          }
+        });
       }
       std::vector<std::pair<double, size_t>> r(cur.size());
       for (size_t s = 0; s < cur.size(); ++s) {
@@ -524,6 +531,12 @@ int plan_kernelize(PlanImpl* p) {
     max_states = std::max<uint64_t>(max_states, cur.size());
   }
   // final: pack every state's open kernels, keep the cheapest
+  c.cm.discover([&]() {
+    for (const State& st : cur) {
+      int32_t dummy = -1;
+      pack(c, st.ks, false, &dummy);
+    }
+  });
   size_t best = 0;
   double best_cost = INF;
   for (size_t s = 0; s < cur.size(); ++s) {

@@ -488,14 +488,15 @@ int launch_m(const V2Params& P, int n, cudaStream_t s) {
 
 }  // namespace
 
-int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, float2* psi, int n, uint64_t hi, cudaStream_t s) {
+int launch_jit(cudaKernel_t k, const ShmProgramV2& pg, int blocks_per_sm, float2* psi, int n, uint64_t hi,
+               cudaStream_t s) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int m = pg.m;
-  const size_t smem = sizeof(float2) * pad_size(m);
+  const size_t smem = (size_t)pg.jit_smem;
   const int threads = 1 << (m - kRegBits);
-  const int bps = 1 << (kMaxShmActive - m);  // the kernels' launch bounds
+  const int bps = std::max(1, blocks_per_sm);
   unsigned long long nb = 1ull << (n - m);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms * bps);
   unsigned long long hiv = hi;

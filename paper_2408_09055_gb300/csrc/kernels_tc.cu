@@ -48,6 +48,9 @@ struct TcParams {
   uint64_t fixed;  // target and column qubits
   int8_t targets[kTcK];
   int8_t cols[8];
+  // fault injection for tests: > 0 makes the MMA thread first wait this
+  // many ns on a barrier that nothing signals, so the launch gives up
+  uint64_t stall_ns;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
   float* Bop = smem;  // stage s: hi at s*NOP*B_FLOATS, lo after it
   float2* Raw = reinterpret_cast<float2*>(smem + ST * NOP * B_FLOATS);  // BULK raw ring
   __shared__ __align__(8) uint64_t bar_full[ST], bar_empty[ST], bar_accf[2], bar_acce[2], bar_fin;
-  __shared__ __align__(8) uint64_t bar_rfull[RS], bar_rempty[RS];
+  __shared__ __align__(8) uint64_t bar_rfull[RS], bar_rempty[RS], bar_never;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_all;
   __shared__ unsigned long long rowoff[kTcDim];
@@ -254,6 +257,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
                    "r"(32 * kDrainWarps) : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_fin)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_never)) : "memory");
     for (int r = 0; r < RS; ++r) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_rfull[r])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_rempty[r])),
@@ -488,7 +492,26 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
     // ---- MMA issue ----
     constexpr uint32_t ID = idesc_tf32<N>();
     uint32_t it = 0;
-    for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x, ++it) {
+    uint64_t bt = blockIdx.x;
+    if (P.stall_ns) {  // injected fault: no arrival ever completes this phase
+      const unsigned long long t0 = global_ns();
+      for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(&bar_never)), "r"(0u)
+            : "memory");
+        if (done) break;
+        if (global_ns() - t0 > P.stall_ns) {
+          fail();
+          bt = nb;  // nothing is issued to the tensor pipe
+          break;
+        }
+      }
+    }
+    for (; bt < nb; bt += gridDim.x, ++it) {
       const uint32_t s = it % ST, ph = (it / ST) & 1u, a = it & 1u, pa = (it >> 1) & 1u;
       if (!mbar_wait_or_abort(smem_u32(&bar_full[s]), ph, &abort_all) ||
           !mbar_wait_or_abort(smem_u32(&bar_acce[a]), pa ^ 1u, &abort_all)) {
@@ -586,9 +609,9 @@ float tf32_round_host(float x) {
 
 // W for a 2^6 x 2^6 complex unitary (row-major complex64) as the kernel's
 // tensor-memory A operand: 128 x 128 row-major, hi part, then (3xTF32) lo.
-void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out) {
+// out: tc_weight_floats(x3) floats.
+void tc_prepare_weights_into(const float* u, bool x3, float* out) {
   const int D = kTcDim, R = kTcKR;
-  out->assign((x3 ? 2 : 1) * R * R, 0.0f);
   for (int m = 0; m < R; ++m)
     for (int kk = 0; kk < R; ++kk) {
       // M index 2r + (0: real, 1: imaginary output part); K index 2c + (0:
@@ -600,18 +623,40 @@ void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out) {
       else w = (kk & 1) ? ur : ui;
       const float hi = tf32_round_host(w);
       const uint32_t o = (uint32_t)(m * R + kk);  // row-major: row m goes to TMEM lane m
-      (*out)[o] = hi;
-      if (x3) (*out)[R * R + o] = tf32_round_host(w - hi);
+      out[o] = hi;
+      if (x3) out[R * R + o] = tf32_round_host(w - hi);
     }
 }
 
-int tc_check_error(bool clear) {
+void tc_prepare_weights(const float* u, bool x3, std::vector<float>* out) {
+  out->assign(tc_weight_floats(x3), 0.0f);
+  tc_prepare_weights_into(u, x3, out->data());
+}
+
+static std::atomic<uint64_t> g_tc_stall_ns{0};
+
+void tc_set_stall(uint64_t ns) { g_tc_stall_ns.store(ns); }
+
+// launches per load-path variant (TcVariant), for tests that must know which
+// path ran
+static std::atomic<uint64_t> g_tc_launches[kTcVariants];
+
+void tc_launch_counts(uint64_t* out, int cap) {
+  for (int v = 0; v < kTcVariants && v < cap; ++v) out[v] = g_tc_launches[v].load();
+}
+
+// Reads the device's expired-wait flag in stream order (after the work
+// queued on s), clearing it when asked.  QS_ETIMEDOUT when it was set.
+int tc_check_error(cudaStream_t s, bool clear) {
   int v = 0;
-  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
   if (v && clear) {
-    int z = 0;
-    cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+    const int z = 0;
+    e = cudaMemcpyToSymbolAsync(g_tc_error, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
   }
   return v ? QS_ETIMEDOUT : QS_OK;
 }
@@ -625,6 +670,7 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
   P.psi = a.psi;
   P.w = reinterpret_cast<const float*>(a.u);
   P.n = a.n;
+  P.stall_ns = g_tc_stall_ns.load();
   P.fixed = 0;
   for (int j = 0; j < kTcK; ++j) {
     P.targets[j] = (int8_t)a.targets[j];
@@ -641,10 +687,8 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
     P.fixed |= 1ull << P.cols[j];
     if (P.cols[j] != j) P.contig = 0;
   }
-  if (a.n > 32) {  // amplitude offsets need 64 bits
-    if (x3) return launch_tc<6, true, 3, true>(P, s);
-    return launch_tc<6, false, 6, true>(P, s);
-  }
+  int rc;
+  TcVariant v;
   // Bulk-staged loads pay off only when a tile's rows lie in many different
   // 2 MiB pages (five or more targets at qubit 18 or above: 32-64 pages per
   // tile, beyond what the address translation caches hold), where they
@@ -652,12 +696,19 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
   // register path is faster (3.1 against 4.0 ms).
   int high = 0;
   for (int j = 0; j < kTcK; ++j) high += a.targets[j] >= 18;
-  if (P.contig && cb == 6 && high >= 5) {
-    if (x3) return launch_tc<6, true, 2, false, true, 2>(P, s);
-    return launch_tc<6, false, 3, false, true, 3>(P, s);
+  if (a.n > 32) {  // amplitude offsets need 64 bits
+    v = kTcWide;
+    rc = x3 ? launch_tc<6, true, 3, true>(P, s) : launch_tc<6, false, 6, true>(P, s);
+  } else if (P.contig && cb == 6 && high >= 5) {
+    v = kTcBulk;
+    rc = x3 ? launch_tc<6, true, 2, false, true, 2>(P, s) : launch_tc<6, false, 3, false, true, 3>(P, s);
+  } else {
+    v = kTcRegister;
+    if (x3) rc = cb == 5 ? launch_tc<5, true, 3, false>(P, s) : launch_tc<6, true, 3, false>(P, s);
+    else rc = cb == 5 ? launch_tc<5, false, 6, false>(P, s) : launch_tc<6, false, 6, false>(P, s);
   }
-  if (x3) return cb == 5 ? launch_tc<5, true, 3, false>(P, s) : launch_tc<6, true, 3, false>(P, s);
-  return cb == 5 ? launch_tc<5, false, 6, false>(P, s) : launch_tc<6, false, 6, false>(P, s);
+  if (rc == QS_OK) g_tc_launches[v].fetch_add(1);
+  return rc;
 }
 
 }  // namespace qs

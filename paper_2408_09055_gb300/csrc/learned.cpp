@@ -6,8 +6,8 @@
 #include <bit>
 #include <cmath>
 #include <cstring>
-#include <string>
-#include <unordered_map>
+#include <limits>
+#include <vector>
 
 #include "internal.hpp"
 
@@ -26,13 +26,85 @@ void kernel_features(int n, const KStat& s, bool fusion, uint64_t exec_mask, flo
   f[43] = s.ng / 64.0f;
 }
 
+// What a prediction depends on, packed into five words: the executed qubit
+// mask, the per-type gate counts, the insular and total gate counts, and the
+// kernel type.
+struct LKey {
+  uint64_t w[5];
+  bool operator==(const LKey& o) const { return std::memcmp(w, o.w, sizeof w) == 0; }
+};
+static_assert(QS_NUM_GATE_TYPES == 10, "key layout holds ten gate counts");
+
+// Memo of predictions: open addressing with linear probing, power-of-two
+// capacity, at most half full.  A NaN value marks a key whose prediction is
+// queued in the current batch.
+struct Memo {
+  std::vector<LKey> keys;
+  std::vector<double> vals;
+  std::vector<uint8_t> used;
+  size_t count = 0;
+  static uint64_t hash(const LKey& k) {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+    for (uint64_t x : k.w) {
+      h ^= x + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+      h ^= h >> 31;
+      h *= 0xBF58476D1CE4E5B9ull;
+    }
+    return h ^ (h >> 29);
+  }
+  void grow() {
+    const size_t cap = keys.empty() ? 1024 : 2 * keys.size();
+    std::vector<LKey> ok;
+    std::vector<double> ov;
+    std::vector<uint8_t> ou;
+    ok.swap(keys);
+    ov.swap(vals);
+    ou.swap(used);
+    keys.assign(cap, LKey{});
+    vals.assign(cap, 0.0);
+    used.assign(cap, 0);
+    count = 0;
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (ou[i]) *slot(ok[i], nullptr) = ov[i];
+  }
+  // room for `extra` more keys without growing: slot pointers taken after
+  // this stay valid for the next `extra` insertions
+  void reserve(size_t extra) {
+    while (2 * (count + extra) > keys.size()) grow();
+  }
+  // the value slot of k, inserting it (value NaN) when absent; *inserted
+  // tells which
+  double* slot(const LKey& k, bool* inserted) {
+    if (2 * (count + 1) > keys.size()) grow();
+    const size_t mask = keys.size() - 1;
+    for (size_t i = hash(k) & mask;; i = (i + 1) & mask) {
+      if (!used[i]) {
+        used[i] = 1;
+        keys[i] = k;
+        vals[i] = std::numeric_limits<double>::quiet_NaN();
+        ++count;
+        if (inserted) *inserted = true;
+        return &vals[i];
+      }
+      if (keys[i] == k) {
+        if (inserted) *inserted = false;
+        return &vals[i];
+      }
+    }
+  }
+};
+
 struct LearnedCost {
   const PlanImpl* p = nullptr;
   qs_mlp* mlp = nullptr;
   int n = 0;
   uint64_t low = 0;
   int fuse_kmin = 1;
-  std::unordered_map<std::string, double> memo;
+  Memo memo;
+  // discovery mode: a miss records the kernel (for one batched inference)
+  // and reads as infeasible instead of running an inference of its own
+  bool collect = false;
+  std::vector<std::pair<KStat, bool>> want;
   cudaStream_t stream = nullptr;
   float* dx = nullptr;
   float* dy = nullptr;
@@ -53,14 +125,12 @@ uint64_t exec_mask(const LearnedCost* lc, const KStat& s, bool fusion) {
   return widen_mask(a, lc->n, std::min(lc->n, std::max(std::popcount(a), 10)));
 }
 
-std::string key_of(const KStat& s, bool fusion, uint64_t mask) {
-  std::string k(1 + 8 + 2 * (QS_NUM_GATE_TYPES + 2), '\0');
-  char* w = k.data();
-  w[0] = fusion ? 1 : 0;
-  std::memcpy(w + 1, &mask, 8);
-  std::memcpy(w + 9, s.cnt, 2 * QS_NUM_GATE_TYPES);
-  std::memcpy(w + 9 + 2 * QS_NUM_GATE_TYPES, &s.nins, 2);
-  std::memcpy(w + 11 + 2 * QS_NUM_GATE_TYPES, &s.ng, 2);
+LKey key_of(const KStat& s, bool fusion, uint64_t mask) {
+  LKey k{};
+  k.w[0] = mask;
+  std::memcpy(&k.w[1], s.cnt, 16);  // counts of types 0..7
+  k.w[3] = (uint64_t)s.cnt[8] | ((uint64_t)s.cnt[9] << 16) | ((uint64_t)s.nins << 32) | ((uint64_t)s.ng << 48);
+  k.w[4] = fusion ? 1 : 0;
   return k;
 }
 
@@ -149,40 +219,66 @@ void learned_destroy(LearnedCost* lc) {
 }
 
 void learned_prefetch(LearnedCost* lc, const std::vector<std::pair<KStat, bool>>& ks) {
-  std::vector<std::string> keys;
-  std::unordered_map<std::string, int> pending;
+  // keys new to the memo get a NaN slot (so a repeat in this batch is
+  // skipped) and a feature row; one inference fills them
+  std::vector<double*> pending;
+  lc->memo.reserve(ks.size());  // no growth below: the queued slot pointers stay valid
   for (const auto& [s, fusion] : ks) {
-    uint64_t m = exec_mask(lc, s, fusion);
-    std::string k = key_of(s, fusion, m);
-    if (lc->memo.count(k) || pending.count(k)) continue;
-    if (ensure_cap(lc, (int)keys.size() + 1) != QS_OK) break;
-    pending.emplace(k, (int)keys.size());
-    kernel_features(lc->n, s, fusion, m, lc->hx + keys.size() * QS_MLP_FEATURES);
-    keys.push_back(std::move(k));
+    const uint64_t m = exec_mask(lc, s, fusion);
+    bool fresh = false;
+    double* v = lc->memo.slot(key_of(s, fusion, m), &fresh);
+    if (!fresh && !std::isnan(*v)) continue;  // known (a NaN slot was queued by discovery)
+    *v = 0.0;  // claimed by this batch: a repeat below is skipped
+    if (ensure_cap(lc, (int)pending.size() + 1) != QS_OK) {
+      *v = 1e30;  // never left unfilled; the status below fails the plan
+      if (lc->status == QS_OK) lc->status = QS_ENOMEM;
+      break;
+    }
+    kernel_features(lc->n, s, fusion, m, lc->hx + pending.size() * QS_MLP_FEATURES);
+    pending.push_back(v);
   }
-  if (keys.empty()) return;
-  int rc = infer(lc, (int)keys.size());
-  if (rc != QS_OK) {
-    if (lc->status == QS_OK) lc->status = rc;
-    return;
-  }
-  for (size_t i = 0; i < keys.size(); ++i) lc->memo.emplace(keys[i], to_cost(lc, lc->hy[i]));
+  if (pending.empty()) return;
+  int rc = infer(lc, (int)pending.size());
+  if (rc != QS_OK && lc->status == QS_OK) lc->status = rc;
+  for (size_t i = 0; i < pending.size(); ++i) *pending[i] = rc == QS_OK ? to_cost(lc, lc->hy[i]) : 1e30;
+}
+
+void learned_collect_begin(LearnedCost* lc) {
+  lc->collect = true;
+  lc->want.clear();
+}
+
+bool learned_collect_end(LearnedCost* lc) {
+  lc->collect = false;
+  if (lc->want.empty()) return false;
+  std::vector<std::pair<KStat, bool>> w;
+  w.swap(lc->want);
+  learned_prefetch(lc, w);
+  return true;
 }
 
 double learned_cost(LearnedCost* lc, const KStat& s, bool fusion) {
-  uint64_t m = exec_mask(lc, s, fusion);
-  std::string k = key_of(s, fusion, m);
-  auto it = lc->memo.find(k);
-  if (it != lc->memo.end()) return it->second;
+  const uint64_t m = exec_mask(lc, s, fusion);
+  const LKey key = key_of(s, fusion, m);
+  if (lc->collect) {
+    bool fresh = false;
+    double* v = lc->memo.slot(key, &fresh);
+    if (!fresh && !std::isnan(*v)) return *v;
+    if (fresh) lc->want.push_back({s, fusion});  // NaN until the batch fills it
+    return 1e30;
+  }
+  bool fresh = false;
+  double* v = lc->memo.slot(key, &fresh);
+  if (!fresh && !std::isnan(*v)) return *v;
   kernel_features(lc->n, s, fusion, m, lc->hx);
   int rc = infer(lc, 1);
   if (rc != QS_OK) {
     if (lc->status == QS_OK) lc->status = rc;
+    *v = 1e30;
     return 1e30;
   }
-  double v = to_cost(lc, lc->hy[0]);
-  lc->memo.emplace(std::move(k), v);
-  return v;
+  *v = to_cost(lc, lc->hy[0]);
+  return *v;
 }
 
 }  // namespace qs

@@ -1,10 +1,12 @@
 // Allocation-free variant of qs_apply_fused (see include/qsim.h).
 //
-// qs_apply_fused stages the caller's unitary in device memory it allocates
-// per call (cudaMallocAsync).  This entry point stages it instead in a fixed
-// file-scope device array, so it never allocates.  Host code cannot use the
-// array's name as a device address: the address is looked up once per device
-// with cudaGetSymbolAddress and cached.
+// qs_apply_fused stages what the fused kernel reads -- the caller's unitary
+// (FP32) or the tensor-core weights prepared from it (TF32, 3xTF32) -- in
+// device memory it allocates per call (cudaMallocAsync).  This entry point
+// stages it instead in a fixed file-scope device array, so it never
+// allocates device memory.  Host code cannot use the array's name as a
+// device address: the address is looked up once per device with
+// cudaGetSymbolAddress and cached.
 #include <mutex>
 
 #include "internal.hpp"
@@ -15,6 +17,9 @@ namespace {
 
 constexpr int kStaticFuseMax = 7;  // widest unitary accepted: 2^7 x 2^7
 constexpr size_t kStaticUElems = size_t(1) << (2 * kStaticFuseMax);  // 128 KiB of complex64
+// the 3xTF32 weights (hi and lo parts of the 128 x 128 real block) fill it exactly
+static_assert(tc_weight_floats(true) * sizeof(float) <= kStaticUElems * sizeof(float2),
+              "tensor-core weights exceed the static staging array");
 
 // Staging buffer for the unitary, shared by every call on a device; it keeps
 // the last call's matrix.
@@ -22,6 +27,10 @@ static __device__ __align__(256) float2 g_static_u[kStaticUElems];
 
 std::mutex g_static_mu;
 float2* g_static_addr[64] = {nullptr};  // device address of g_static_u, per device
+// host-side scratch for the widened unitary and its tensor-core weights
+// (guarded by g_static_mu): static, so a call allocates no host memory either
+float g_static_uw[2 << (2 * kTcTargets)];
+float g_static_w[tc_weight_floats(true)];
 
 // Set-up, once per device with that device current: the device address of
 // the staging array.
@@ -61,9 +70,6 @@ extern "C" int qs_apply_fused_static(float* state, int32_t n, const int32_t* tar
   int rc = static_u_address(&u_dev);
   if (rc != QS_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = sizeof(float2) << (2 * k);
-  cudaError_t e = cudaMemcpyAsync(u_dev, u_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_status(e);
   FusedLaunch a;
   a.psi = reinterpret_cast<float2*>(state);
   a.n = n;
@@ -71,7 +77,29 @@ extern "C" int qs_apply_fused_static(float* state, int32_t n, const int32_t* tar
   for (int j = 0; j < kMaxFuse; ++j) a.targets[j] = j < k ? targets[j] : -1;
   a.u = u_dev;
   a.precision = precision;
+  {
+    // the host scratch is released once the copy has read it: a copy from
+    // pageable memory returns after the source has been consumed
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    const float* src = u_host;
+    size_t bytes = sizeof(float2) << (2 * k);
+    if (precision != QS_PREC_FP32) {
+      // as qs_apply_fused: widen to the kernel's 6 targets with the lowest
+      // unused qubits (U (x) I), then the TF32 hi (and lo) weights
+      if (k > kTcTargets || n < kTcTargets + 5) return QS_EUNSUPPORTED;
+      widen_unitary(u_host, k, kTcTargets, g_static_uw);
+      widen_targets(n, k, kTcTargets, a.targets);
+      a.k = kTcTargets;
+      const bool x3 = precision == QS_PREC_TF32X3;
+      tc_prepare_weights_into(g_static_uw, x3, g_static_w);
+      src = g_static_w;
+      bytes = tc_weight_floats(x3) * sizeof(float);
+    }
+    cudaError_t e = cudaMemcpyAsync(u_dev, src, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   rc = launch_fused(a, s);
   if (rc == QS_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == QS_OK) rc = tc_check_error(s, true);
   return rc;
 }

@@ -11,6 +11,7 @@
 //    Cost(C[j..i]) over contiguous segments.
 //  * KERNELIZE   -- Alg. 3 with Alg. 4 (kernelize.cpp).
 #include <algorithm>
+#include <cstdlib>
 #include <bit>
 #include <chrono>
 #include <cmath>
@@ -365,7 +366,18 @@ uint64_t widen_mask(uint64_t mask, int n, int want) {
   return mask;
 }
 
+// Lowest qubits added to every shared-memory kernel's tile (while the tile
+// stays within kTileCap qubits), so the load and store phases move longer
+// contiguous runs: QSIM_TILE_LOW overrides the default.
+static int tile_low_qubits() {
+  const char* e = std::getenv("QSIM_TILE_LOW");
+  if (e && *e >= '0' && *e <= '9') return std::min(8, std::atoi(e));
+  return 0;
+}
+constexpr int kTileCap = 13;
+
 int compile_programs(PlanImpl* p) {
+  const int tile_low = tile_low_qubits();
   const size_t K = p->kernels.size();
   p->shm.assign(K, ShmProgram());
   p->fused.assign(K, FusedProgram());
@@ -375,6 +387,9 @@ int compile_programs(PlanImpl* p) {
     if (k.type == QS_KERNEL_SHM) {
       int want = std::min(p->n, std::max(std::min(10, kMaxShmActive), std::popcount(k.mask)));
       k.mask = widen_mask(k.mask, p->n, want);
+      for (int q = 0; q < std::min(tile_low, p->n); ++q)
+        if (!((k.mask >> q) & 1) && std::popcount(k.mask) < kTileCap && ((p->exec_limit >> q) & 1))
+          k.mask |= 1ull << q;
       if (std::popcount(k.mask) > kMaxShmActive) return QS_EPLAN;
       if (!compile_shm(p, k, &p->shm[i])) return QS_EPLAN;
       if (p->opts.shm_variant != 1 && p->shm[i].m >= kMinPhasedM)

@@ -77,6 +77,13 @@ struct ShmProgramV2 {
   std::vector<PhaseMap> maps;
   int act[kMaxPhasedM];      // physical qubit of local bit j
   int jit_module = -1;       // index of the JIT module holding this kernel, -1: none
+  // launch shape of the specialised kernel (set by jit_source): dynamic
+  // shared memory in bytes, the CTAs per SM its launch bounds ask for, and
+  // its batch-load form (0 direct loads, 1 cp.async prefetch into a separate
+  // staging buffer, 2 prefetch into the exchange tile after the last exchange)
+  int jit_smem = 0;
+  int jit_min_blocks = 1;
+  int jit_prefetch = 0;
 };
 
 // Padded shared-memory layout of the JIT kernels: one spare amplitude per 16,

@@ -126,6 +126,9 @@ def _load():
         "qs_remap": ([vp, vp, i32, ip, vp], ctypes.c_int),
         "qs_apply_fused": ([vp, i32, ip, i32, fp, i32, vp], ctypes.c_int),
         "qs_apply_fused_static": ([vp, i32, ip, i32, fp, i32, vp], ctypes.c_int),
+        "qs_sync": ([vp], ctypes.c_int),
+        "qs_debug_tc_stall": ([i64], ctypes.c_int),
+        "qs_debug_tc_launch_counts": ([ctypes.POINTER(ctypes.c_uint64), i32], i32),
         "qs_mlp_create": ([i32, i32, u64, ctypes.POINTER(vp)], ctypes.c_int),
         "qs_mlp_free": ([vp], None),
         "qs_mlp_num_params": ([vp], i64),
@@ -420,6 +423,27 @@ def qs_apply_fused_static(state_ptr: int, n: int, targets, u: np.ndarray, precis
     check(_lib.qs_apply_fused_static(state_ptr, n, t, len(targets),
                                      uu.view(np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                      precision, _stream_ptr(stream)), "qs_apply_fused_static")
+
+
+def qs_sync(stream=None):
+    """Synchronises the stream; raises QsError (QS_ETIMEDOUT, QS_ECUDA) for
+    errors of the work queued on it."""
+    check(_lib.qs_sync(_stream_ptr(stream)), "qs_sync")
+
+
+def qs_debug_tc_stall(limit_us: int):
+    """Test-only: later tensor-core launches give up after limit_us on a
+    barrier nothing signals (0: off)."""
+    check(_lib.qs_debug_tc_stall(int(limit_us)), "qs_debug_tc_stall")
+
+
+def qs_debug_tc_launch_counts() -> dict:
+    """Tensor-core fused launches so far, per load path (test-only)."""
+    out = (ctypes.c_uint64 * 3)()
+    nv = _lib.qs_debug_tc_launch_counts(out, 3)
+    if nv < 0:
+        check(nv, "qs_debug_tc_launch_counts")
+    return {"register": int(out[0]), "bulk": int(out[1]), "wide": int(out[2])}
 
 
 def _fp(a: np.ndarray):
