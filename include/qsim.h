@@ -141,6 +141,13 @@ typedef struct qs_plan_opts {
   int64_t stager_budget;  /* QS_STAGER_EXACT: work limit in gate visits
                              (<= 0: 2^28, about a second)                     */
   int32_t stager;         /* enum qs_stager (staged plans only)                */
+  int32_t insular_x;      /* staged plans: 1 treats X as insular (Definition 2:
+                             anti-diagonal) -- an X on a regional qubit is a
+                             relabelling of the stage's chunks, the stage's
+                             later controls and diagonal factors on that qubit
+                             are conjugated (App. A.2's control flip), and
+                             chunk c is written back to host chunk c ^ (the
+                             flipped qubits).  0: X is non-insular.         */
 } qs_plan_opts;
 
 /* Fills `opts` with the defaults (Kernelize, analytic cost, FP32, |A| <= 13,
@@ -223,6 +230,16 @@ int64_t qs_plan_kernel_program(const qs_plan* plan, uint64_t k, uint32_t* words,
  * gates sharing a qubit that is not insular in both, circuit order kept.
  * QS_OK or QS_EPLAN.                                                        */
 int qs_plan_validate(const qs_plan* plan, const qs_gate* gates, uint64_t ngates);
+
+/* Insular X gates of a staged plan (qs_plan_opts.insular_x; App. A.2): the
+ * logical regional qubits whose values the stage flips (*frame: the stage's
+ * stored chunk c is written back to host chunk c with those bits flipped)
+ * and the circuit indices of the X gates it executes that way, in circuit
+ * order (*num_flips of them; flip_gates may be NULL, else it needs
+ * cap >= *num_flips entries).  Unstaged plans: 0 and none.  QS_EINVAL for a
+ * bad stage or cap.                                                          */
+int qs_plan_stage_frame(const qs_plan* plan, int32_t stage, uint64_t* frame, int32_t* flip_gates,
+                        int64_t cap, int64_t* num_flips);
 
 /* Stage `stage` of a plan (0..num_stages-1; an unstaged plan has one stage
  * holding every qubit): the mask of its local qubits, its gate count and
@@ -397,6 +414,13 @@ int qs_mlp_set_params(qs_mlp* mlp, const float* host_in, uint64_t n);
  * the loss into loss_out (host, or NULL).  Synchronises the stream.        */
 int qs_mlp_gradient(qs_mlp* mlp, const float* x_device, const float* t_device, int32_t batch,
                     float* grad_out, float* loss_out, void* stream);
+/* Loss of qs_mlp_gradient and qs_mlp_train_step: the expectile tau of
+ * ln(time) -- weight 2 tau on samples the network underestimates, 2 (1 -
+ * tau) on those it overestimates, times the squared error.  tau = 0.5 (the
+ * default) is the mean squared error; tau > 0.5 trains a pessimistic model,
+ * so a planner that minimises predicted cost finds fewer kernels whose cost
+ * the network underestimates.  QS_EINVAL unless 0 < tau < 1.                */
+int qs_mlp_set_expectile(qs_mlp* mlp, float tau);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch's gradient. */
 int qs_mlp_train_step(qs_mlp* mlp, const float* x_device, const float* t_device, int32_t batch,
                       float lr, float* loss_out, void* stream);

@@ -53,12 +53,16 @@ def loss(theta, x, t, F, H) -> float:
     return float(np.mean((y - np.asarray(t, dtype=np.float64)) ** 2))
 
 
-def gradient(theta, x, t, F, H):
-    """Backpropagation of the mean squared error; returns (loss, grad)."""
+def gradient(theta, x, t, F, H, tau=0.5):
+    """Backpropagation of the expectile loss mean(w (y - t)^2), w = 2 tau
+    where y < t and 2 (1 - tau) elsewhere (tau = 0.5: the mean squared
+    error); returns (loss, grad)."""
     p = unpack(np.asarray(theta, dtype=np.float64), F, H)
     y, (x, z1, h1, z2, h2) = forward(theta, x, F, H)
     B = x.shape[0]
-    dy = 2.0 * (y - np.asarray(t, dtype=np.float64)) / B
+    d = y - np.asarray(t, dtype=np.float64)
+    w = np.where(d < 0, 2.0 * tau, 2.0 * (1.0 - tau))
+    dy = 2.0 * w * d / B
     g = {}
     g["W3"] = h2.T @ dy
     g["b3"] = np.array([dy.sum()])
@@ -68,7 +72,7 @@ def gradient(theta, x, t, F, H):
     dh1 = (dh2 @ p["W2"].T) * (z1 > 0)
     g["W1"] = x.T @ dh1
     g["b1"] = dh1.sum(axis=0)
-    return float(np.mean((y - t) ** 2)), pack(g, F, H)
+    return float(np.mean(w * d ** 2)), pack(g, F, H)
 
 
 class Adam:

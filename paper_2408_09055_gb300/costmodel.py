@@ -144,7 +144,7 @@ def _time_specs(n, specs, reps, st, s, threads, log=None):
 
 
 def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC_TF32X3, reps=3,
-           epochs=300, threads=None, log=print, weight=4, entangling_share=0.67):
+           epochs=300, threads=None, log=print, weight=4, entangling_share=0.67, tau=0.5):
     """Active refinement: plan freshly seeded workload circuits with the
     learned cost (Kernelize, fused kernels in `precision`), time exactly the
     kernels those plans chose, add them to the data and retrain.  A planner
@@ -193,7 +193,7 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
             [X[base[0]]] + [Xr[rtr]] * weight, [y[base[0]]] + [yr[rtr]] * weight,
             [X[base[1]], Xr[rva]], [y[base[1]], yr[rva]], [X[base[2]], Xr[rte]], [y[base[2]], yr[rte]])]
         net, metrics = train_parts((parts[0], parts[1]), (parts[2], parts[3]), (parts[4], parts[5]),
-                                   epochs=epochs, seed=seed)
+                                   epochs=epochs, seed=seed, tau=tau)
         history.append({"kernels": int(len(yn)), "fused": int(sum(kinds)), "pred_over_actual": bias})
         if log:
             log(f"refinement round {r + 1}: +{len(yn)} kernels ({sum(kinds)} fused), "
@@ -205,6 +205,49 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
     return net, np.concatenate([X, Xr]), np.concatenate([y, yr]), metrics, test_idx
 
 
+def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, stream=None, log=None):
+    """The learned model's plan-level gain: for each seed, the mixed circuit
+    (5000 gates) planned by Kernelize with the analytic table and with the
+    learned cost under the same options (|A| <= shm_max, fused 3xTF32
+    kernels allowed), each plan timed on a resident n-qubit state (the
+    median of `reps` runs after one warm-up).  Returns per-seed circuit
+    times and kernel counts and the gain sum(analytic) / sum(learned)."""
+    import torch
+    from synth import circuits as C
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    st = Q.State(n, buf.data_ptr())
+    out = {"n": n, "gates": gates, "shm_max_active": shm_max, "seeds": [], "analytic_ms": [], "learned_ms": [],
+           "analytic_kernels": [], "learned_kernels": [], "learned_fused": []}
+
+    def timed(plan):
+        st.set_zero(s)
+        st.run(plan, s)
+        timer = Q.Timer(plan, reps)
+        for _ in range(reps):
+            st.run_timed(plan, timer, s)
+        ms, runs = timer.read()
+        return float(np.sum(ms)) / runs
+
+    for seed in seeds:
+        g = C.mixed_circuit(n, gates, seed)
+        base = dict(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3, fuse_kmax=6, shm_max_active=shm_max)
+        pa = Q.Plan(n, g, Q.default_opts(**base))
+        pl = Q.Plan(n, g, Q.default_opts(mlp=net, **base))
+        out["seeds"].append(int(seed))
+        out["analytic_ms"].append(timed(pa))
+        out["learned_ms"].append(timed(pl))
+        out["analytic_kernels"].append(int(pa.stats().num_kernels))
+        out["learned_kernels"].append(int(pl.stats().num_kernels))
+        out["learned_fused"].append(int(pl.stats().num_fused))
+        if log:
+            log(f"seed {seed}: analytic {out['analytic_ms'][-1]:.2f} ms ({out['analytic_kernels'][-1]} kernels), "
+                f"learned {out['learned_ms'][-1]:.2f} ms ({out['learned_kernels'][-1]} kernels, "
+                f"{out['learned_fused'][-1]} fused)")
+    out["gain"] = float(np.sum(out["analytic_ms"]) / np.sum(out["learned_ms"]))
+    return out
+
+
 def split(count, seed=0, fractions=(0.8, 0.1, 0.1)):
     perm = np.random.default_rng(seed).permutation(count)
     a = int(fractions[0] * count)
@@ -212,19 +255,20 @@ def split(count, seed=0, fractions=(0.8, 0.1, 0.1)):
     return perm[:a], perm[a:b], perm[b:]
 
 
-def train(X, y, hidden=128, epochs=200, batch=256, lr=1e-3, seed=0, stream=None, log=None):
+def train(X, y, hidden=128, epochs=200, batch=256, lr=1e-3, seed=0, stream=None, log=None, tau=0.5):
     """Trains a fresh network on (X, y) with an 80/10/10 split; returns the
     network and a metrics dict (MSE of ln time; mean |relative error| of
     time) for the train, validation and test parts."""
     tr, va, te = split(len(y), seed)
     return train_parts((X[tr], y[tr]), (X[va], y[va]), (X[te], y[te]), hidden, epochs, batch, lr, seed,
-                       stream, log)
+                       stream, log, tau)
 
 
 def train_parts(train_set, val_set, test_set, hidden=128, epochs=200, batch=256, lr=1e-3, seed=0,
-                stream=None, log=None):
-    """Trains on train_set, keeps the epoch with the best validation MSE,
-    reports metrics on all three (X, y) parts."""
+                stream=None, log=None, tau=0.5):
+    """Trains on train_set with the expectile-tau loss of ln(time) (tau =
+    0.5: mean squared error; larger: pessimistic), keeps the epoch with the
+    best validation loss, reports metrics on all three (X, y) parts."""
     import torch
     Xtr, ytr = train_set
     dev = torch.device("cuda")
@@ -232,6 +276,7 @@ def train_parts(train_set, val_set, test_set, hidden=128, epochs=200, batch=256,
     yd = torch.from_numpy(np.ascontiguousarray(ytr, dtype=np.float32)).to(dev)
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     net = Q.Mlp(Xtr.shape[1], hidden, seed)
+    net.set_expectile(tau)
     # centre the output on the mean target so training starts close
     theta = net.get_params()
     theta[-1] = float(np.mean(ytr))
@@ -246,13 +291,13 @@ def train_parts(train_set, val_set, test_set, hidden=128, epochs=200, batch=256,
             tb = yd.index_select(0, idx).contiguous()
             net.train_step(xb.data_ptr(), tb.data_ptr(), len(idx), lr, s)
         if ep % 10 == 9 or ep == epochs - 1:
-            v = evaluate(net, val_set[0], val_set[1], stream=s)["mse"]
+            v = evaluate(net, val_set[0], val_set[1], stream=s, tau=tau)["loss"]
             if v < best:
                 best, best_theta = v, net.get_params()
             if log:
                 log(f"epoch {ep + 1}: validation MSE {v:.4f}")
     net.set_params(best_theta)
-    metrics = {name: evaluate(net, part[0], part[1], stream=s) for name, part in
+    metrics = {name: evaluate(net, part[0], part[1], stream=s, tau=tau) for name, part in
                (("train", train_set), ("validation", val_set), ("test", test_set))}
     return net, metrics
 
@@ -268,13 +313,18 @@ def predict(net, X, bf16=True, stream=None) -> np.ndarray:
     return out.cpu().numpy()
 
 
-def evaluate(net, X, y, bf16=True, stream=None) -> dict:
+def evaluate(net, X, y, bf16=True, stream=None, tau=0.5) -> dict:
+    """MSE and expectile-tau loss of ln(time), mean and median |relative
+    error| of time, and the mean predicted/actual time ratio."""
     if len(y) == 0:
-        return {"mse": float("nan"), "mean_rel_err": float("nan")}
+        return {"mse": float("nan"), "loss": float("nan"), "mean_rel_err": float("nan")}
     p = predict(net, X, bf16, stream)
-    rel = np.abs(np.exp(p - y) - 1.0)
-    return {"mse": float(np.mean((p - y) ** 2)), "mean_rel_err": float(np.mean(rel)),
-            "median_rel_err": float(np.median(rel))}
+    d = p - y
+    rel = np.abs(np.exp(d) - 1.0)
+    w = np.where(d < 0, 2 * tau, 2 * (1 - tau))
+    return {"mse": float(np.mean(d ** 2)), "loss": float(np.mean(w * d ** 2)),
+            "mean_rel_err": float(np.mean(rel)), "median_rel_err": float(np.median(rel)),
+            "pred_over_actual": float(np.mean(np.exp(d)))}
 
 
 def save(net, path=MODEL_PATH, meta=None) -> None:
@@ -302,20 +352,24 @@ def main(argv=None):
     ap.add_argument("--out", default=MODEL_PATH)
     ap.add_argument("--refine-rounds", type=int, default=6)
     ap.add_argument("--data", default=None, help="reuse timed kernels saved by an earlier run")
+    ap.add_argument("--tau", type=float, default=0.5,
+                    help="expectile of ln(time) the network learns (0.5: mean squared error)")
     a = ap.parse_args(argv)
     if a.data:
         d = np.load(a.data)
         X, y, meta = d["X"], d["y"], json.loads(str(d["meta"]))
     else:
         X, y, meta = generate(count=a.count, seed=a.seed)
-    net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print)
+    net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print, tau=a.tau)
     test_idx = split(len(y), a.seed)[2]
     if a.refine_rounds:
-        net, X, y, metrics, test_idx = refine(net, X, y, rounds=a.refine_rounds, seed=a.seed, epochs=a.epochs)
+        net, X, y, metrics, test_idx = refine(net, X, y, rounds=a.refine_rounds, seed=a.seed, epochs=a.epochs,
+                                              tau=a.tau)
         meta["refine_rounds"] = a.refine_rounds
         meta["count"] = int(len(y))
     np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, test_idx=test_idx, meta=json.dumps(meta))
     meta["metrics"] = metrics
+    meta["tau"] = a.tau
     save(net, a.out, meta)
     print(json.dumps(meta))
 

@@ -208,6 +208,7 @@ void qs_plan_opts_default(qs_plan_opts* o) {
   o->mlp = nullptr;
   o->stager_budget = 0;
   o->stager = QS_STAGER_BEAM;
+  o->insular_x = 0;
 }
 
 }  // extern "C"
@@ -241,10 +242,55 @@ static int build_impl(PlanImpl& P, int n, const qs_gate* gates, const int32_t* i
 static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o) {
   PlanImpl& P = p->impl;
   const int n = P.n, L = o.local_qubits;
-  int rc = stage_circuit(P.gates, n, L, o.stager, o.stager_budget, &p->stages, &p->staging_optimal);
+  // with insular_x the stager sees X as insular (anti-diagonal, Definition 2)
+  std::vector<Gate> sg = P.gates;
+  if (o.insular_x)
+    for (Gate& x : sg)
+      if (x.type == QS_X) x.nimask = 0;
+  int rc = stage_circuit(sg, n, L, o.stager, o.stager_budget, &p->stages, &p->staging_optimal);
   if (rc != QS_OK) return rc;
+  double phase = 0;  // global phase of the conjugated gates (radians)
   for (size_t si = 0; si < p->stages.size(); ++si) {
     Stage& st = p->stages[si];
+    // the stage's gates on the stored state: an X on a regional qubit flips
+    // the frame f (the stored chunks are the logical ones relabelled by f);
+    // a later gate is conjugated by X^f (App. A.2's control flip)
+    std::vector<qs_gate> sgates;
+    st.src.clear();
+    st.flips.clear();
+    uint64_t f = 0;
+    for (int32_t i : st.gates) {
+      const qs_gate& x = gates[i];
+      if (o.insular_x && x.type == QS_X && !((st.local >> x.q[0]) & 1)) {
+        f ^= 1ull << x.q[0];
+        st.flips.push_back(i);
+        continue;
+      }
+      const size_t first = sgates.size();
+      if (!conjugate_by_x(x, f, &sgates, &phase)) return QS_EPLAN;  // f is regional: insular qubits only
+      for (size_t j = first; j < sgates.size(); ++j) st.src.push_back(j == first ? i : -1);
+    }
+    st.frame = f;
+    const double two_pi = 6.283185307179586;
+    phase = std::fmod(phase, two_pi);
+    if (si + 1 == p->stages.size() && std::fabs(phase) > 1e-15 && std::fabs(std::fabs(phase) - two_pi) > 1e-15) {
+      // e^{i a} = P(a) X P(a) X on a local qubit, P(a) = U3(0, 0, a) exactly
+      const int q = st.order[0];
+      qs_gate pg{}, xg{};
+      pg.type = QS_U3;
+      pg.nq = 1;
+      pg.q[0] = q;
+      pg.q[1] = -1;
+      pg.p[2] = phase;
+      xg.type = QS_X;
+      xg.nq = 1;
+      xg.q[0] = q;
+      xg.q[1] = -1;
+      for (const qs_gate& y : {pg, xg, pg, xg}) {
+        sgates.push_back(y);
+        st.src.push_back(-1);
+      }
+    }
     st.plan = std::make_unique<PlanImpl>();
     PlanImpl& S = *st.plan;
     S.n = n;
@@ -252,12 +298,15 @@ static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o)
     S.opts.local_qubits = 0;
     S.cost = P.cost;
     S.exec_limit = (1ull << L) - 1;
-    rc = build_impl(S, n, gates, st.gates.data(), st.pos.data(), st.gates.size());
+    rc = build_impl(S, n, sgates.data(), nullptr, st.pos.data(), sgates.size());
     if (rc != QS_OK) return rc;
     for (size_t k = 0; k < S.kernels.size(); ++k) {
       Kernel K = S.kernels[k];
       K.stage = (int32_t)si;
-      for (auto& g : K.gates) g = st.gates[g];
+      std::vector<int32_t> ids;  // circuit indices of the kernel's gates
+      for (int32_t g : K.gates)
+        if (st.src[g] >= 0) ids.push_back(st.src[g]);
+      K.gates.swap(ids);
       uint64_t m = 0;
       for (int b = 0; b < n; ++b)
         if ((K.mask >> b) & 1) m |= 1ull << st.order[b];
@@ -277,7 +326,39 @@ static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o)
 // local in its stage, and the stage's programs are those of its gates.
 static int validate_staged(const qs_plan* p) {
   const PlanImpl& P = p->impl;
-  int rc = validate_plan(&P);
+  int rc;
+  if (!P.opts.insular_x) {
+    rc = validate_plan(&P);
+  } else {
+    // Theorem 2 with X insular (Definition 2): the X gates a stage executes
+    // as relabellings count as placed at the start of their stage, and
+    // gates that pass an X on an insular qubit are its conjugates
+    PlanImpl V;
+    V.n = P.n;
+    V.gates = P.gates;
+    for (Gate& x : V.gates)
+      if (x.type == QS_X) x.nimask = 0;
+    size_t k = 0;
+    for (size_t si = 0; si < p->stages.size(); ++si) {
+      const Stage& st = p->stages[si];
+      if (st.frame & st.local) return QS_EPLAN;
+      uint64_t f = 0;
+      for (int32_t i : st.flips) {
+        if (i < 0 || (size_t)i >= P.gates.size() || P.gates[i].type != QS_X) return QS_EPLAN;
+        if ((st.local >> P.gates[i].q0) & 1) return QS_EPLAN;
+        f ^= 1ull << P.gates[i].q0;
+      }
+      if (f != st.frame) return QS_EPLAN;
+      if (!st.flips.empty()) {
+        Kernel F;
+        F.gates = st.flips;
+        V.kernels.push_back(std::move(F));
+      }
+      for (; k < P.kernels.size() && P.kernels[k].stage == (int32_t)si; ++k) V.kernels.push_back(P.kernels[k]);
+    }
+    if (k != P.kernels.size()) return QS_EPLAN;
+    rc = validate_plan(&V);
+  }
   if (rc != QS_OK) return rc;
   if (P.kernels.size() != p->kmap.size()) return QS_EPLAN;
   int32_t last = 0;
@@ -555,6 +636,26 @@ int qs_plan_validate(const qs_plan* p, const qs_gate* gates, uint64_t ngates) {
     if (g.type != h.type || g.q0 != h.q0 || g.q1 != h.q1) return QS_EPLAN;
   }
   return p->stages.empty() ? validate_plan(&P) : validate_staged(p);
+}
+
+int qs_plan_stage_frame(const qs_plan* p, int32_t stage, uint64_t* frame, int32_t* flip_gates, int64_t cap,
+                        int64_t* num_flips) {
+  if (!p || !frame || !num_flips) return QS_EINVAL;
+  const int32_t ns = p->stages.empty() ? 1 : (int32_t)p->stages.size();
+  if (stage < 0 || stage >= ns) return QS_EINVAL;
+  if (p->stages.empty()) {
+    *frame = 0;
+    *num_flips = 0;
+    return QS_OK;
+  }
+  const Stage& st = p->stages[stage];
+  *frame = st.frame;
+  *num_flips = (int64_t)st.flips.size();
+  if (flip_gates) {
+    if (cap < (int64_t)st.flips.size()) return QS_EINVAL;
+    std::copy(st.flips.begin(), st.flips.end(), flip_gates);
+  }
+  return QS_OK;
 }
 
 int qs_plan_stage(const qs_plan* p, int32_t stage, uint64_t* local_mask, int64_t* num_gates,
@@ -856,12 +957,14 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
   cudaError_t e = cudaPointerGetAttributes(&at, host_state);
   if (e != cudaSuccess) return cuda_status(e);
   if (at.type != cudaMemoryTypeHost) return QS_EINVAL;
+  bool framed = false;  // a stage writes its chunks back relabelled: pairs need two buffers
+  for (const Stage& st : plan->stages) framed |= st.frame != 0;
   int nbuf = 0;
   float2* dbuf = static_cast<float2*>(device_buffer);
   if (dbuf) {
     if (reinterpret_cast<uintptr_t>(dbuf) & 255) return QS_EINVAL;
     nbuf = (int)std::min<uint64_t>(kMaxChunkBuffers, buffer_bytes / chunk_bytes);
-    if (nbuf < 1) return QS_EINVAL;
+    if (nbuf < (framed ? 2 : 1)) return QS_EINVAL;
   }
   // device programs of every stage, before any work is queued
   std::vector<PlanImpl*> plans;
@@ -889,6 +992,10 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
     fail(cudaStreamCreateWithFlags(&ss[b], cudaStreamNonBlocking));
   for (int b = 0; b <= nbuf && rc == QS_OK; ++b)
     fail(cudaEventCreateWithFlags(&evs[b], cudaEventDisableTiming));
+  // per buffer: its chunk's copy-in and kernels are queued (paired chunks)
+  cudaEvent_t inev[kMaxChunkBuffers] = {};
+  for (int b = 0; b < nbuf && rc == QS_OK; ++b)
+    fail(cudaEventCreateWithFlags(&inev[b], cudaEventDisableTiming));
   if (tm) {
     tm->recorded = false;
     if (rc == QS_OK) fail(cudaEventRecord(tm->ev[0], user));
@@ -973,12 +1080,23 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
       return c;
     };
     std::vector<std::pair<uint64_t, uint64_t>> units;  // (source chunk, unit index)
-    for (uint64_t c = 0; c < nch && rc == QS_OK; ++c, ++gchunk) {
-      const int b = (int)(gchunk % (uint64_t)nbuf);
-      const cudaStream_t s = ss[b];
-      float2* d = dbuf + (uint64_t(b) << L);
-      const uint64_t hbase = staged ? deposit(c, L, n - L) : 0;
-      cudaEvent_t* te = tm ? &tm->ev[1 + 4 * (si * nch + c)] : nullptr;
+    // the stage's frame in chunk-index bits: the stored chunk c holds the
+    // logical chunk c ^ fc, so it is written back there (insular X gates)
+    uint64_t fc = 0;
+    if (staged)
+      for (int k = L; k < n; ++k)
+        if ((st->frame >> st->order[k]) & 1) fc |= 1ull << (k - L);
+    struct Slot {
+      uint64_t c = 0;
+      int b = 0;
+    };
+    // copy-in (after a stage boundary: unit by unit, each after the previous
+    // stage's chunk it comes from) and the stage's kernels
+    auto load_run = [&](const Slot& x) {
+      const cudaStream_t s = ss[x.b];
+      float2* d = dbuf + (uint64_t(x.b) << L);
+      const uint64_t hbase = staged ? deposit(x.c, L, n - L) : 0;
+      cudaEvent_t* te = tm ? &tm->ev[1 + 4 * (si * nch + x.c)] : nullptr;
       if (te && rc == QS_OK) fail(cudaEventRecord(te[0], s));
       if (!prev) {
         copy(d, hbase, s, true);
@@ -1001,11 +1119,39 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
         }
       }
       if (te && rc == QS_OK) fail(cudaEventRecord(te[1], s));
-      if (rc == QS_OK) rc = run_kernels(plans[si], dcs[si], d, L, c << L, s, nullptr);
+      if (rc == QS_OK) rc = run_kernels(plans[si], dcs[si], d, L, x.c << L, s, nullptr);
       if (te && rc == QS_OK) fail(cudaEventRecord(te[2], s));
-      copy(d, hbase, s, false);
+    };
+    // copy-out of chunk x.c to host chunk x.c ^ fc
+    auto store = [&](const Slot& x) {
+      const cudaStream_t s = ss[x.b];
+      float2* d = dbuf + (uint64_t(x.b) << L);
+      const uint64_t to = x.c ^ fc;
+      copy(d, staged ? deposit(to, L, n - L) : 0, s, false);
+      cudaEvent_t* te = tm ? &tm->ev[1 + 4 * (si * nch + x.c)] : nullptr;
       if (te && rc == QS_OK) fail(cudaEventRecord(te[3], s));
-      if (multi && rc == QS_OK) fail(cudaEventRecord(done[si & 1][c], s));
+      if (multi && rc == QS_OK) fail(cudaEventRecord(done[si & 1][to], s));
+    };
+    for (uint64_t c = 0; c < nch && rc == QS_OK; ++c) {
+      if (!fc) {
+        Slot x{c, (int)(gchunk++ % (uint64_t)nbuf)};
+        load_run(x);
+        store(x);
+        continue;
+      }
+      if ((c ^ fc) < c) continue;  // handled with its partner
+      // a pair: each copy-out overwrites the partner's host chunk, so it
+      // waits for the partner's copy-in
+      Slot x{c, (int)(gchunk++ % (uint64_t)nbuf)};
+      Slot y{c ^ fc, (int)(gchunk++ % (uint64_t)nbuf)};
+      load_run(x);
+      if (rc == QS_OK) fail(cudaEventRecord(inev[x.b], ss[x.b]));
+      load_run(y);
+      if (rc == QS_OK) fail(cudaEventRecord(inev[y.b], ss[y.b]));
+      if (rc == QS_OK) fail(cudaStreamWaitEvent(ss[x.b], inev[y.b], 0));
+      if (rc == QS_OK) fail(cudaStreamWaitEvent(ss[y.b], inev[x.b], 0));
+      store(x);
+      store(y);
     }
   }
   for (auto& v : done)
@@ -1020,6 +1166,8 @@ static int run_plan_host_impl(const qs_plan* plan, float* host_state, void* devi
     if (ss[b]) cudaStreamDestroy(ss[b]);
   for (int b = 0; b <= nbuf; ++b)
     if (evs[b]) cudaEventDestroy(evs[b]);
+  for (int b = 0; b < nbuf; ++b)
+    if (inev[b]) cudaEventDestroy(inev[b]);
   if (tm && rc == QS_OK) tm->recorded = true;
   return rc;
 }

@@ -78,6 +78,81 @@ void gate_matrix(const Gate& g, double* m) {
   }
 }
 
+// X on the qubits of `flip` conjugates a gate: g' = X^f g X^f, written as
+// gates of the table and a global phase (App. A.2: an anti-diagonal gate
+// moved past a control flips the control; a diagonal factor swaps its
+// entries).  Only qubits on which g is insular may be flipped (controls and
+// diagonal qubits); the parts commute, so their order is free.
+//   RZ(t) on q            -> RZ(-t)
+//   CX, control flipped   -> CX, then X on the target
+//   CZ(a,b), a flipped    -> CZ, Z_b = e^{i pi/2} RZ_b(pi); both: CZ RZ_a(pi) RZ_b(pi)
+//   CP(t)(a,b), a flipped -> CP(-t), P_b(t) = e^{i t/2} RZ_b(t); both:
+//                            CP(t) RZ_a(-t) RZ_b(-t)
+// Returns false when g is not insular on every flipped qubit.
+bool conjugate_by_x(const qs_gate& g, uint64_t flip, std::vector<qs_gate>* out, double* phase) {
+  const uint64_t fa = (flip >> g.q[0]) & 1ull;
+  const uint64_t fb = g.nq == 2 ? ((flip >> g.q[1]) & 1ull) : 0ull;
+  if (!fa && !fb) {
+    out->push_back(g);
+    return true;
+  }
+  auto rz = [&](int q, double t) {
+    qs_gate r{};
+    r.type = QS_RZ;
+    r.nq = 1;
+    r.q[0] = q;
+    r.q[1] = -1;
+    r.p[0] = t;
+    out->push_back(r);
+  };
+  const double pi = 3.14159265358979323846;
+  switch (g.type) {
+    case QS_RZ: {
+      rz(g.q[0], -g.p[0]);
+      return true;
+    }
+    case QS_CX: {  // q[0] control (insular), q[1] target (never flipped)
+      if (fb) return false;
+      out->push_back(g);
+      qs_gate x{};
+      x.type = QS_X;
+      x.nq = 1;
+      x.q[0] = g.q[1];
+      x.q[1] = -1;
+      out->push_back(x);
+      return true;
+    }
+    case QS_CZ: {
+      out->push_back(g);
+      if (fa && fb) {
+        rz(g.q[0], pi);
+        rz(g.q[1], pi);
+      } else {
+        rz(fa ? g.q[1] : g.q[0], pi);
+        *phase += 0.5 * pi;
+      }
+      return true;
+    }
+    case QS_CP: {
+      const double t = g.p[0];
+      qs_gate c = g;
+      if (fa && fb) {
+        out->push_back(c);
+        rz(g.q[0], -t);
+        rz(g.q[1], -t);
+      } else {
+        c.p[0] = -t;
+        out->push_back(c);
+        rz(fa ? g.q[1] : g.q[0], t);
+        *phase += 0.5 * t;
+      }
+      return true;
+    }
+    default:
+      return false;
+  }
+}
+
 int make_gate(const qs_gate& in, int n, Gate* out) {
   if (in.type < 0 || in.type >= QS_NUM_GATE_TYPES) return QS_EINVAL;
   const int k = gate_arity(in.type);

@@ -36,6 +36,9 @@ void gate_matrix(const Gate& g, double* m);
 // Validates a public gate and fills the internal one.  Returns QS_OK/EINVAL.
 int make_gate(const qs_gate& in, int n, Gate* out);
 bool gate_is_diagonal(int type);
+// g' = X^flip g X^flip as table gates appended to out, plus a global phase
+// added to *phase (radians); false when g is not insular on a flipped qubit.
+bool conjugate_by_x(const qs_gate& g, uint64_t flip, std::vector<qs_gate>* out, double* phase);
 
 struct LearnedCost;  // learned.cpp
 // Discovery: between begin and end, a prediction not yet known reads as
@@ -189,6 +192,14 @@ struct Stage {
   std::vector<int32_t> order;    // position -> logical qubit (inverse of pos)
   int run_log = 0;               // local qubits 0..run_log-1: contiguous host runs
   std::unique_ptr<PlanImpl> plan;
+  // X gates on regional qubits (qs_plan_opts.insular_x): circuit indices of
+  // the X gates the stage executes as a relabelling, and the regional
+  // qubits flipped at its end (chunk c is written back to host chunk c ^ frame)
+  std::vector<int32_t> flips;
+  uint64_t frame = 0;
+  // per gate of the stage's own plan: its circuit index, -1 for the extra
+  // gates of a conjugated gate and for the closing phase gates
+  std::vector<int32_t> src;
 };
 // local qubits the stager may choose freely; the rest, L - kStageSlots
 // lowest qubits, stay local in every stage so host runs are 2^(L-8) long

@@ -25,6 +25,9 @@ struct qs_mlp {
   __nv_bfloat16* wbf = nullptr;  // BF16 copy of the parameters
   bool bf_stale = true;
   int64_t step = 0;
+  // loss: expectile of ln(time), weight 2 tau on underestimates (y < t) and
+  // 2 (1 - tau) on overestimates; tau = 0.5 is the mean squared error
+  float tau = 0.5f;
   // activations for a batch (grown on demand)
   int cap = 0;
   float *z1 = nullptr, *z2 = nullptr, *y = nullptr, *dz = nullptr, *dh = nullptr, *loss = nullptr;
@@ -66,9 +69,11 @@ __global__ void linear_fwd(const float* in, int B, int I, const float* W, const 
   out[idx] = acc;
 }
 
-// output layer: y[b] = relu(z2[b]) . W3 + b3; dz[b] = 2 (y - t) / B; loss partial
+// output layer: y[b] = relu(z2[b]) . W3 + b3; with d = y - t and the
+// expectile weight w = 2 tau (d < 0) or 2 (1 - tau): loss partial w d^2 / B,
+// dz[b] = 2 w d / B
 __global__ void output_fwd_bwd(const float* z2, int B, int H, const float* W3, const float* b3,
-                               const float* t, float* y, float* dz, float* loss) {
+                               const float* t, float tau, float* y, float* dz, float* loss) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   float acc = b3[0];
@@ -76,8 +81,9 @@ __global__ void output_fwd_bwd(const float* z2, int B, int H, const float* W3, c
   y[b] = acc;
   if (t) {
     const float d = acc - t[b];
-    dz[b] = 2.0f * d / (float)B;
-    atomicAdd(loss, d * d / (float)B);
+    const float w = 2.0f * (d < 0.0f ? tau : 1.0f - tau);
+    dz[b] = 2.0f * w * d / (float)B;
+    atomicAdd(loss, w * d * d / (float)B);
   }
 }
 
@@ -201,7 +207,8 @@ int run_gradient(qs_mlp* M, const float* x, const float* t, int B, cudaStream_t 
   cudaMemsetAsync(M->loss, 0, sizeof(float), s);
   linear_fwd<<<blocks((size_t)B * H), kT, 0, s>>>(x, B, F, th + o.W1, th + o.b1, H, false, M->z1);
   linear_fwd<<<blocks((size_t)B * H), kT, 0, s>>>(M->z1, B, H, th + o.W2, th + o.b2, H, true, M->z2);
-  output_fwd_bwd<<<blocks(B), kT, 0, s>>>(M->z2, B, H, th + o.W3, th + o.b3, t, M->y, M->dz, M->loss);
+  output_fwd_bwd<<<blocks(B), kT, 0, s>>>(M->z2, B, H, th + o.W3, th + o.b3, t, M->tau, M->y, M->dz,
+                                          M->loss);
   float* g = M->grad;
   float* dh2 = M->dh;
   float* dh1 = M->dh + (size_t)B * H;
@@ -268,6 +275,12 @@ void qs_mlp_free(qs_mlp* M) {
 }
 
 int64_t qs_mlp_num_params(const qs_mlp* M) { return M ? (int64_t)M->np : QS_EINVAL; }
+
+int qs_mlp_set_expectile(qs_mlp* M, float tau) {
+  if (!M || !(tau > 0.0f && tau < 1.0f)) return QS_EINVAL;
+  M->tau = tau;
+  return QS_OK;
+}
 
 int qs_mlp_shape(const qs_mlp* M, int32_t* features, int32_t* hidden) {
   if (!M || !features || !hidden) return QS_EINVAL;
@@ -341,7 +354,8 @@ int qs_mlp_forward(qs_mlp* M, const float* x, int32_t batch, float* y, int32_t b
   const float* th = M->theta;
   linear_fwd<<<blocks((size_t)batch * M->H), kT, 0, s>>>(x, batch, M->F, th + o.W1, th + o.b1, M->H, false, M->z1);
   linear_fwd<<<blocks((size_t)batch * M->H), kT, 0, s>>>(M->z1, batch, M->H, th + o.W2, th + o.b2, M->H, true, M->z2);
-  output_fwd_bwd<<<blocks(batch), kT, 0, s>>>(M->z2, batch, M->H, th + o.W3, th + o.b3, nullptr, y, nullptr, nullptr);
+  output_fwd_bwd<<<blocks(batch), kT, 0, s>>>(M->z2, batch, M->H, th + o.W3, th + o.b3, nullptr, 0.5f, y, nullptr,
+                                              nullptr);
   return cuda_status(cudaGetLastError());
 }
 

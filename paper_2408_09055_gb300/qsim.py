@@ -56,7 +56,8 @@ class qs_plan_opts(ctypes.Structure):
                 ("attach_single", ctypes.c_int32), ("local_qubits", ctypes.c_int32),
                 ("shm_variant", ctypes.c_int32),
                 ("cost", ctypes.POINTER(qs_cost_table)), ("mlp", ctypes.c_void_p),
-                ("stager_budget", ctypes.c_int64), ("stager", ctypes.c_int32)]
+                ("stager_budget", ctypes.c_int64), ("stager", ctypes.c_int32),
+                ("insular_x", ctypes.c_int32)]
 
 
 class qs_plan_stats(ctypes.Structure):
@@ -113,6 +114,8 @@ def _load():
         "qs_run_plan_host_timed": ([vp, vp, vp, u64, vp, vp], ctypes.c_int),
         "qs_host_timer_read": ([vp, dp, u64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "qs_host_timer_free": ([vp], None),
+        "qs_plan_stage_frame": ([vp, i32, ctypes.POINTER(ctypes.c_uint64), ip, i64, ctypes.POINTER(ctypes.c_int64)],
+                                ctypes.c_int),
         "qs_plan_stage": ([vp, i32, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int64), ip, ip],
                           ctypes.c_int),
         "qs_timer_create": ([vp, u64, ctypes.POINTER(vp)], ctypes.c_int),
@@ -136,6 +139,7 @@ def _load():
         "qs_mlp_get_params": ([vp, fp, u64], ctypes.c_int),
         "qs_mlp_set_params": ([vp, fp, u64], ctypes.c_int),
         "qs_mlp_gradient": ([vp, vp, vp, i32, fp, fp, vp], ctypes.c_int),
+        "qs_mlp_set_expectile": ([vp, ctypes.c_float], ctypes.c_int),
         "qs_mlp_train_step": ([vp, vp, vp, i32, ctypes.c_float, fp, vp], ctypes.c_int),
         "qs_mlp_forward": ([vp, vp, i32, vp, i32, vp], ctypes.c_int),
         "qs_kernel_features": ([i32, vp, u64, i32, u64, fp], ctypes.c_int),
@@ -271,6 +275,17 @@ class Plan:
                                  ctypes.byref(cnt)), "qs_plan_stage")
         return {"local_mask": int(mask.value), "num_gates": int(ng.value),
                 "first_kernel": int(first.value), "num_kernels": int(cnt.value)}
+
+    def stage_frame(self, i: int) -> tuple[int, list[int]]:
+        """qs_plan_stage_frame: (flipped regional qubits as a mask, circuit
+        indices of the X gates the stage executes as a relabelling)."""
+        fr, cnt = ctypes.c_uint64(), ctypes.c_int64()
+        check(_lib.qs_plan_stage_frame(self.h, int(i), ctypes.byref(fr), None, 0, ctypes.byref(cnt)),
+              "qs_plan_stage_frame")
+        ids = (ctypes.c_int32 * max(1, cnt.value))()
+        check(_lib.qs_plan_stage_frame(self.h, int(i), ctypes.byref(fr), ids, cnt.value, ctypes.byref(cnt)),
+              "qs_plan_stage_frame")
+        return int(fr.value), [int(ids[k]) for k in range(cnt.value)]
 
     def stages(self) -> list[dict]:
         return [self.stage(i) for i in range(self.stats().num_stages)]
@@ -483,6 +498,9 @@ class Mlp:
         check(_lib.qs_mlp_gradient(self.h, x_ptr, t_ptr, int(batch), _fp(g), _fp(loss), _stream_ptr(stream)),
               "qs_mlp_gradient")
         return float(loss[0]), g
+
+    def set_expectile(self, tau: float) -> None:
+        check(_lib.qs_mlp_set_expectile(self.h, float(tau)), "qs_mlp_set_expectile")
 
     def train_step(self, x_ptr: int, t_ptr: int, batch: int, lr: float, stream=None) -> float:
         loss = np.zeros(1, dtype=np.float32)

@@ -46,6 +46,24 @@ def test_gradient_and_forward_match_oracle(H):
     assert np.max(np.abs(y.cpu().numpy() - ref_y)) <= 1e-4 * max(1.0, np.max(np.abs(ref_y)))
 
 
+def test_expectile_gradient_matches_oracle():
+    # the pessimistic loss (weight 2 tau on underestimates) on the GPU
+    # against the FP64 network, element by element
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    H, tau = 64, 0.8
+    net = Q.Mlp(F, H, seed=7)
+    net.set_expectile(tau)
+    theta = net.get_params().astype(np.float64)
+    x, t = _data(257, 11)
+    loss, g = net.gradient(_dev(x).data_ptr(), _dev(t).data_ptr(), len(t))
+    ref_loss, ref_g = OM.gradient(theta, x.astype(np.float64), t.astype(np.float64), F, H, tau=tau)
+    assert abs(loss - ref_loss) <= 1e-4 * max(1.0, ref_loss)
+    np.testing.assert_allclose(g, ref_g, rtol=1e-3, atol=1e-5 * float(np.max(np.abs(ref_g))))
+    with pytest.raises(Q.QsError):
+        net.set_expectile(1.0)
+
+
 def _bf16(a):
     """Round-to-nearest-even to bfloat16, kept in float64."""
     u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)

@@ -194,3 +194,51 @@ def test_alloc_state_starts_at_zero_and_runs_a_plan():
     assert v[0] == 1 and np.count_nonzero(v) == 1
     st.run(Q.Plan(n, g), s)
     assert_close_state(st.read(stream=s), sim.apply(n, g))
+
+
+def _insular_x_rule_circuit(n, L, seed):
+    # dense gates keep the low L qubits local; X gates on the two highest
+    # (regional) qubits, then every insular use of them: controls, CZ, CP,
+    # RZ, both flipped together; later dense gates make them local
+    rng = np.random.default_rng(seed)
+    a, b = n - 1, n - 2
+    items = [(C.H, q, None, 0, 0, 0) for q in range(L)]
+    items += [(C.X, a, None, 0, 0, 0), (C.CZ, a, 2, 0, 0, 0), (C.CP, 5, a, rng.uniform(0, 6.28), 0, 0),
+              (C.CX, a, 3, 0, 0, 0), (C.RZ, a, None, rng.uniform(0, 6.28), 0, 0),
+              (C.X, b, None, 0, 0, 0), (C.CZ, a, b, 0, 0, 0), (C.CP, b, a, rng.uniform(0, 6.28), 0, 0),
+              (C.CX, b, 7, 0, 0, 0), (C.RZ, b, None, rng.uniform(0, 6.28), 0, 0)]
+    items += [(C.U3, q, None, *rng.uniform(0, 6.28, 3)) for q in range(L)]
+    items += [(C.H, a, None, 0, 0, 0), (C.H, b, None, 0, 0, 0), (C.CX, a, 0, 0, 0, 0), (C.CZ, b, 4, 0, 0, 0)]
+    return C.make_gates(items)
+
+
+@pytest.mark.parametrize("nbuf", [None, 2, 3, 4])
+@pytest.mark.parametrize("case", ["rules", "mixed"])
+def test_insular_x_stages_match_oracle(case, nbuf):
+    # X gates on regional qubits run as chunk relabellings (App. A.2): chunks
+    # are written back in pairs to their partners' host chunks
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    if case == "rules":
+        n, L = 17, 12
+        g = _insular_x_rule_circuit(n, L, nbuf or 0)
+    else:
+        n, L = 19, 14
+        g = C.mixed_circuit(n, 900, 11)
+    plan = Q.Plan(n, g, local_qubits=L, insular_x=1, shm_max_active=12)
+    frames = [plan.stage_frame(i)[0] for i in range(plan.stats().num_stages)]
+    assert any(frames)
+    psi0 = random_state(n, 3 + (nbuf or 0))
+    got = run_host(plan, n, psi0, nbuf)
+    assert_close_state(got, sim.apply(n, g, psi0.copy()))
+
+
+def test_insular_x_stages_need_two_chunk_buffers():
+    need_gpu()
+    from paper_2408_09055_gb300 import qsim as Q
+    n, L = 17, 12
+    g = _insular_x_rule_circuit(n, L, 0)
+    plan = Q.Plan(n, g, local_qubits=L, insular_x=1, shm_max_active=12)
+    with pytest.raises(Q.QsError) as ei:
+        run_host(plan, n, None, 1)
+    assert ei.value.status == Q.QS_EINVAL
