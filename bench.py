@@ -213,20 +213,21 @@ def reference_arm(args):
     return 0
 
 
-def make_plan(Q, gates, which, shm_max=13, algo=None, n=N_QUBITS, forced_low=4):
+def make_plan(Q, gates, which, shm_max=13, algo=None, n=N_QUBITS, forced_low=4, insular_x=1):
     if which.startswith("F-"):  # every kernel fused (k = 6), in the given precision
         prec = {"F-FP32": Q.QS_PREC_FP32, "F-TF32": Q.QS_PREC_TF32, "F-TF32X3": Q.QS_PREC_TF32X3}[which]
         cost = Q.default_cost_table()
         for k in range(16):
             cost.fuse_cost[k] = 1.0
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=prec, fuse_kmax=6, fuse_kmin=6,
-                              cost=cost)
+                              cost=cost, insular_x=insular_x)
         return Q.Plan(n, gates, opts), f"{which}: Kernelize, every kernel a fused 2^6 unitary"
     if which == "B":  # learned-cost Kernelize, fused kernels on tensor cores in 3xTF32
         from paper_2408_09055_gb300 import costmodel as CM
         net, _ = CM.load()
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3,
-                              shm_max_active=shm_max, fuse_kmax=6, mlp=net, forced_low=forced_low)
+                              shm_max_active=shm_max, fuse_kmax=6, mlp=net, forced_low=forced_low,
+                              insular_x=insular_x)
         if algo == "ordered":
             opts.algo = Q.QS_ALGO_ORDERED
         plan = Q.Plan(n, gates, opts)
@@ -236,12 +237,12 @@ def make_plan(Q, gates, which, shm_max=13, algo=None, n=N_QUBITS, forced_low=4):
     if which == "A" and algo == "ordered":
         opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, cost_kind=Q.QS_COST_ANALYTIC,
                               precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0,
-                              forced_low=forced_low)
+                              forced_low=forced_low, insular_x=insular_x)
         label = "A': analytic-cost OrderedKernelize, shared-memory kernels, FP32"
     elif which == "A":
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, cost_kind=Q.QS_COST_ANALYTIC,
                               precision=Q.QS_PREC_FP32, shm_max_active=shm_max, fuse_kmax=0,
-                              forced_low=forced_low)
+                              forced_low=forced_low, insular_x=insular_x)
         label = "A: analytic-cost Kernelize, shared-memory kernels, FP32"
     else:
         raise ValueError(which)
@@ -535,6 +536,8 @@ def main():
     ap.add_argument("--no-error", action="store_true",
                     help="skip the 26-qubit error-against-FP64 leg (rank 0, beside the CPU baseline)")
     ap.add_argument("--shm-max", type=int, default=12)
+    ap.add_argument("--no-insular-x", action="store_true",
+                    help="plan without the Pauli-frame rewrite that makes X insular (App. A.2)")
     ap.add_argument("--forced-low", type=int, default=4,
                     help="lowest qubits forced into every shared-memory kernel (2^f * 8-byte runs)")
     ap.add_argument("--workload", default="mixed", choices=["mixed", "entangling"])
@@ -582,7 +585,9 @@ def main():
     host_in[0] = 1.0
     host_out = torch.zeros(2 << n, dtype=torch.float32).pin_memory()
     gates = workload_gates(args.workload)
-    plan, label = make_plan(Q, gates, args.plan, args.shm_max, args.algo, forced_low=args.forced_low)
+    ix = 0 if args.no_insular_x else 1
+    plan, label = make_plan(Q, gates, args.plan, args.shm_max, args.algo, forced_low=args.forced_low,
+                            insular_x=ix)
     ps = plan.stats()
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     st = Q.State(n, buf.data_ptr())
@@ -658,6 +663,7 @@ def main():
                    "fused_kernels": int(ps.num_fused), "passes": int(ps.num_kernels),
                    "planner_ms": ps.planner_ms, "jit_ms": ps.jit_ms, "shm_max_active": args.shm_max,
                    "forced_low": args.forced_low,
+                   "insular_x": "Pauli-frame rewrite (every X moved to the end, App. A.2)" if ix else "off",
                    "model_cost_ms": ps.cost / 1e3, "l2": "no flush: the 8 GiB state exceeds L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gates_per_s": len(gates) / (value * 1e-3),
@@ -676,7 +682,7 @@ def main():
 
     def arm(g, which, ref_ms=None):
         """One more plan timed the same way on the same state."""
-        p, lab = make_plan(Q, g, which, args.shm_max, args.algo, forced_low=args.forced_low)
+        p, lab = make_plan(Q, g, which, args.shm_max, args.algo, forced_low=args.forced_low, insular_x=ix)
         s_ = p.stats()
         st.set_zero(sp)
         ms, pk, r = time_plan(Q, torch, st, p, args.steps, args.warmup, stream, world)

@@ -106,6 +106,11 @@ typedef struct qs_cost_table {
 
 typedef struct qs_mlp qs_mlp; /* learned cost model, see below */
 
+enum qs_insular_x {
+  QS_INSULAR_X_REWRITE = 1, /* plan the Pauli-frame rewrite of the circuit     */
+  QS_INSULAR_X_STAGED = 2   /* staged plans: X on regional qubits relabels chunks */
+};
+
 typedef struct qs_plan_opts {
   int32_t algo;           /* enum qs_algo                                      */
   int32_t cost_kind;      /* enum qs_cost_kind; LEARNED needs `mlp`            */
@@ -141,13 +146,21 @@ typedef struct qs_plan_opts {
   int64_t stager_budget;  /* QS_STAGER_EXACT: work limit in gate visits
                              (<= 0: 2^28, about a second)                     */
   int32_t stager;         /* enum qs_stager (staged plans only)                */
-  int32_t insular_x;      /* staged plans: 1 treats X as insular (Definition 2:
-                             anti-diagonal) -- an X on a regional qubit is a
-                             relabelling of the stage's chunks, the stage's
-                             later controls and diagonal factors on that qubit
-                             are conjugated (App. A.2's control flip), and
-                             chunk c is written back to host chunk c ^ (the
-                             flipped qubits).  0: X is non-insular.         */
+  int32_t insular_x;      /* bit mask; X is insular (Definition 2: anti-
+                             diagonal).  QS_INSULAR_X_REWRITE: the circuit
+                             is planned as its Pauli-frame rewrite
+                             (qs_insular_x_rewrite): every X moves to the
+                             end, flipping the controls and diagonal factors
+                             it passes (App. A.2), so no X needs an active
+                             qubit before the last kernels; kernel gate
+                             indices refer to the rewritten circuit.
+                             QS_INSULAR_X_STAGED (staged plans): an X on a
+                             regional qubit is a relabelling of the stage's
+                             chunks -- the stage's later controls and
+                             diagonal factors on it are conjugated, and chunk
+                             c is written back to host chunk c ^ (the
+                             flipped qubits), which needs >= 2 chunk buffers.
+                             0: X is non-insular.                           */
 } qs_plan_opts;
 
 /* Fills `opts` with the defaults (Kernelize, analytic cost, FP32, |A| <= 13,
@@ -225,6 +238,18 @@ int64_t qs_plan_kernel_source(const qs_plan* plan, uint64_t k, char* out, uint64
  * no register-phased program (fused kernels, tiles below 2^10).            */
 int64_t qs_plan_kernel_program(const qs_plan* plan, uint64_t k, uint32_t* words, uint64_t cap,
                                int32_t* layout);
+
+/* The circuit an insular-X plan executes (qs_plan_opts.insular_x): the
+ * Pauli-frame rewrite of gates[0 .. ngates).  The stored state is the
+ * circuit's up to a Pauli frame prod_q Z^z X^x and a global phase: an X only
+ * updates the frame; H, CX, CZ and SWAP map it; RZ, RX, RXX, U3 and CP are
+ * conjugated by it (angle signs, CP's control flip with RZ factors); at the
+ * end the frame is applied as X and RZ(pi) gates and the phase as
+ * U3(0,0,a) X U3(0,0,a) X on qubit 0.  The result equals the circuit's state
+ * exactly in exact arithmetic.  *nout = the rewritten gate count; out may be
+ * NULL, else it needs cap >= *nout entries (QS_EINVAL otherwise).        */
+int qs_insular_x_rewrite(int32_t n, const qs_gate* gates, uint64_t ngates, qs_gate* out, uint64_t cap,
+                         uint64_t* nout);
 
 /* Checks Theorem 2 on a plan: every gate exactly once and, for every pair of
  * gates sharing a qubit that is not insular in both, circuit order kept.

@@ -209,7 +209,7 @@ def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, 
     """The learned model's plan-level gain: for each seed, the mixed circuit
     (5000 gates) planned by Kernelize with the analytic table and with the
     learned cost under the same options (|A| <= shm_max, fused 3xTF32
-    kernels allowed), each plan timed on a resident n-qubit state (the
+    kernels allowed, insular X), each plan timed on a resident n-qubit state (the
     median of `reps` runs after one warm-up).  Returns per-seed circuit
     times and kernel counts and the gain sum(analytic) / sum(learned)."""
     import torch
@@ -231,7 +231,8 @@ def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, 
 
     for seed in seeds:
         g = C.mixed_circuit(n, gates, seed)
-        base = dict(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3, fuse_kmax=6, shm_max_active=shm_max)
+        base = dict(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3, fuse_kmax=6, shm_max_active=shm_max,
+                    insular_x=1)
         pa = Q.Plan(n, g, Q.default_opts(**base))
         pl = Q.Plan(n, g, Q.default_opts(mlp=net, **base))
         out["seeds"].append(int(seed))

@@ -244,7 +244,8 @@ static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o)
   const int n = P.n, L = o.local_qubits;
   // with insular_x the stager sees X as insular (anti-diagonal, Definition 2)
   std::vector<Gate> sg = P.gates;
-  if (o.insular_x)
+  const bool relabel = (o.insular_x & QS_INSULAR_X_STAGED) != 0;
+  if (relabel)
     for (Gate& x : sg)
       if (x.type == QS_X) x.nimask = 0;
   int rc = stage_circuit(sg, n, L, o.stager, o.stager_budget, &p->stages, &p->staging_optimal);
@@ -261,7 +262,7 @@ static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o)
     uint64_t f = 0;
     for (int32_t i : st.gates) {
       const qs_gate& x = gates[i];
-      if (o.insular_x && x.type == QS_X && !((st.local >> x.q[0]) & 1)) {
+      if (relabel && x.type == QS_X && !((st.local >> x.q[0]) & 1)) {
         f ^= 1ull << x.q[0];
         st.flips.push_back(i);
         continue;
@@ -327,7 +328,7 @@ static int build_staged(qs_plan* p, const qs_gate* gates, const qs_plan_opts& o)
 static int validate_staged(const qs_plan* p) {
   const PlanImpl& P = p->impl;
   int rc;
-  if (!P.opts.insular_x) {
+  if (!(P.opts.insular_x & QS_INSULAR_X_STAGED)) {
     rc = validate_plan(&P);
   } else {
     // Theorem 2 with X insular (Definition 2): the X gates a stage executes
@@ -456,8 +457,18 @@ static int plan_circuit_impl(int32_t n, const qs_gate* gates, uint64_t ngates, c
   if (o.shm_variant < 0 || o.shm_variant > 3) return QS_EINVAL;
   if (o.local_qubits < 0) return QS_EINVAL;
   if (o.stager != QS_STAGER_BEAM && o.stager != QS_STAGER_EXACT) return QS_EINVAL;
+  if (o.insular_x < 0 || o.insular_x > (QS_INSULAR_X_REWRITE | QS_INSULAR_X_STAGED)) return QS_EINVAL;
   if (o.local_qubits >= n) o.local_qubits = 0;
   const bool staged = o.local_qubits > 0;
+  // insular X: plan the Pauli-frame rewrite of the circuit (no X gate before
+  // its final frame layer)
+  std::vector<qs_gate> rewritten;
+  if (o.insular_x & QS_INSULAR_X_REWRITE) {
+    const int rrc = pauli_frame_rewrite(n, gates, ngates, &rewritten);
+    if (rrc != QS_OK) return rrc;
+    gates = rewritten.data();
+    ngates = rewritten.size();
+  }
   // a chunk holds the widest kernel (a 2^14 tile, a widened fused kernel)
   if (staged && (o.local_qubits < kMinLocalQubits || o.local_qubits < o.shm_max_active ||
                  o.local_qubits < o.forced_low + 2))
@@ -625,9 +636,29 @@ int64_t qs_plan_kernel_program(const qs_plan* p, uint64_t k, uint32_t* words, ui
   return (int64_t)pg.prog.size();
 }
 
+int qs_insular_x_rewrite(int32_t n, const qs_gate* gates, uint64_t ngates, qs_gate* out, uint64_t cap,
+                         uint64_t* nout) {
+  if (!nout || n < 1 || n > kMaxQubits || (ngates && !gates)) return QS_EINVAL;
+  std::vector<qs_gate> r;
+  const int rc = pauli_frame_rewrite(n, gates, ngates, &r);
+  if (rc != QS_OK) return rc;
+  *nout = r.size();
+  if (out) {
+    if (cap < r.size()) return QS_EINVAL;
+    std::copy(r.begin(), r.end(), out);
+  }
+  return QS_OK;
+}
+
 int qs_plan_validate(const qs_plan* p, const qs_gate* gates, uint64_t ngates) {
   if (!p) return QS_EINVAL;
   const PlanImpl& P = p->impl;
+  std::vector<qs_gate> rewritten;  // an insular-X plan executes the rewritten circuit
+  if ((P.opts.insular_x & QS_INSULAR_X_REWRITE) && (ngates == 0 || gates)) {
+    if (pauli_frame_rewrite(P.n, gates, ngates, &rewritten) != QS_OK) return QS_EPLAN;
+    gates = rewritten.data();
+    ngates = rewritten.size();
+  }
   if (ngates != P.gates.size() || (ngates && !gates)) return QS_EPLAN;
   for (uint64_t i = 0; i < ngates; ++i) {
     Gate g;

@@ -153,6 +153,124 @@ bool conjugate_by_x(const qs_gate& g, uint64_t flip, std::vector<qs_gate>* out, 
   }
 }
 
+// Pauli frame (App. A.2's reordering of anti-diagonal insular gates, taken
+// to the end of the circuit).  The stored state s relates to the circuit's
+// state by psi = e^{i a} (prod_q Z_q^{z_q} X_q^{x_q}) s.  An X gate only
+// toggles x_q; a Clifford gate G (H, CX, CZ, SWAP) is applied as it is and
+// maps the frame to G P G^dagger; any other gate G is applied as P^dagger G P
+// (angles of RZ, RX, RXX, U3 change sign, CP's control flip), with the frame
+// unchanged.  At the end the frame is applied as gates: X on x_q, Z = i RZ(pi)
+// on z_q, and the global phase as P(a) X P(a) X on qubit 0, P(a) = U3(0,0,a).
+namespace {
+
+qs_gate mk1(int type, int q, double t0 = 0, double t1 = 0, double t2 = 0) {
+  qs_gate g{};
+  g.type = type;
+  g.nq = 1;
+  g.q[0] = q;
+  g.q[1] = -1;
+  g.p[0] = t0;
+  g.p[1] = t1;
+  g.p[2] = t2;
+  return g;
+}
+
+}  // namespace
+
+int pauli_frame_rewrite(int n, const qs_gate* in, uint64_t count, std::vector<qs_gate>* out) {
+  const double pi = 3.14159265358979323846;
+  std::vector<uint8_t> x(n, 0), z(n, 0);
+  double a = 0;  // global phase, radians
+  out->clear();
+  out->reserve(count + 2 * (size_t)n + 4);
+  for (uint64_t i = 0; i < count; ++i) {
+    const qs_gate& g = in[i];
+    if (g.type < 0 || g.type >= QS_NUM_GATE_TYPES || g.nq != gate_arity(g.type)) return QS_EINVAL;
+    const int q = g.q[0], r = g.nq == 2 ? g.q[1] : -1;
+    if (q < 0 || q >= n || (g.nq == 2 && (r < 0 || r >= n || r == q))) return QS_EINVAL;
+    switch (g.type) {
+      case QS_X:  // X Z^z X^x = (-1)^z Z^z X^(x+1)
+        if (z[q]) a += pi;
+        x[q] ^= 1;
+        break;
+      case QS_H:  // H Z^z X^x H = X^z Z^x = (-1)^(xz) Z^x X^z
+        out->push_back(g);
+        if (x[q] && z[q]) a += pi;
+        std::swap(x[q], z[q]);
+        break;
+      case QS_CX:  // X_c -> X_c X_t, Z_t -> Z_c Z_t; no sign
+        out->push_back(g);
+        x[r] ^= x[q];
+        z[q] ^= z[r];
+        break;
+      case QS_CZ:  // X_a -> X_a Z_b, X_b -> Z_a X_b; sign (-1)^(x_a x_b)
+        out->push_back(g);
+        if (x[q] && x[r]) a += pi;
+        z[q] ^= x[r];
+        z[r] ^= x[q];
+        break;
+      case QS_SWAP:
+        out->push_back(g);
+        std::swap(x[q], x[r]);
+        std::swap(z[q], z[r]);
+        break;
+      case QS_RZ: {  // Z commutes; X: RZ(-t)
+        qs_gate h = g;
+        if (x[q]) h.p[0] = -g.p[0];
+        out->push_back(h);
+        break;
+      }
+      case QS_RX: {  // X commutes; Z: RX(-t)
+        qs_gate h = g;
+        if (z[q]) h.p[0] = -g.p[0];
+        out->push_back(h);
+        break;
+      }
+      case QS_RXX: {  // X's commute; Z on one qubit anticommutes with X X: RXX(-t)
+        qs_gate h = g;
+        if (z[q] ^ z[r]) h.p[0] = -g.p[0];
+        out->push_back(h);
+        break;
+      }
+      case QS_U3: {  // P^dagger U P = X^x Z^z U Z^z X^x
+        double t = g.p[0], ph = g.p[1], la = g.p[2];
+        if (z[q]) {  // Z U3(t, ph, la) Z = U3(t, ph + pi, la + pi)
+          ph += pi;
+          la += pi;
+        }
+        if (x[q]) {  // X U3(t, ph, la) X = e^{i(ph + la)} U3(-t, -ph, -la)
+          a += ph + la;
+          t = -t;
+          ph = -ph;
+          la = -la;
+        }
+        out->push_back(mk1(QS_U3, q, t, ph, la));
+        break;
+      }
+      case QS_CP: {  // Z's commute; X's: the control flip (conjugate_by_x)
+        const uint64_t f = ((uint64_t)x[q] << q) | ((uint64_t)x[r] << r);
+        if (!conjugate_by_x(g, f, out, &a)) return QS_EINVAL;
+        break;
+      }
+      default:
+        return QS_EINVAL;
+    }
+  }
+  for (int q = 0; q < n; ++q)
+    if (x[q]) out->push_back(mk1(QS_X, q));
+  for (int q = 0; q < n; ++q)
+    if (z[q]) {  // Z = e^{i pi/2} RZ(pi)
+      out->push_back(mk1(QS_RZ, q, pi));
+      a += 0.5 * pi;
+    }
+  a = std::remainder(a, 2 * pi);
+  if (std::fabs(a) > 1e-15) {
+    const qs_gate p = mk1(QS_U3, 0, 0.0, 0.0, a), xg = mk1(QS_X, 0);
+    for (const qs_gate& y : {p, xg, p, xg}) out->push_back(y);
+  }
+  return QS_OK;
+}
+
 int make_gate(const qs_gate& in, int n, Gate* out) {
   if (in.type < 0 || in.type >= QS_NUM_GATE_TYPES) return QS_EINVAL;
   const int k = gate_arity(in.type);

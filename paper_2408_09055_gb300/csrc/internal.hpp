@@ -39,6 +39,9 @@ bool gate_is_diagonal(int type);
 // g' = X^flip g X^flip as table gates appended to out, plus a global phase
 // added to *phase (radians); false when g is not insular on a flipped qubit.
 bool conjugate_by_x(const qs_gate& g, uint64_t flip, std::vector<qs_gate>* out, double* phase);
+// The circuit with every X moved to its end through a Pauli frame (exact,
+// global phase included); QS_EINVAL for a malformed gate.
+int pauli_frame_rewrite(int n, const qs_gate* in, uint64_t count, std::vector<qs_gate>* out);
 
 struct LearnedCost;  // learned.cpp
 // Discovery: between begin and end, a prediction not yet known reads as

@@ -38,6 +38,9 @@ class QsError(RuntimeError):
         super().__init__(msg)
 
 
+QS_INSULAR_X_REWRITE, QS_INSULAR_X_STAGED = 1, 2
+
+
 class qs_gate(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("nq", ctypes.c_int32), ("q", ctypes.c_int32 * 2),
                 ("p", ctypes.c_double * 3)]
@@ -101,6 +104,7 @@ def _load():
         "qs_plan_kernel_gates": ([vp, u64, ip, u64], i64),
         "qs_plan_fused_matrix": ([vp, u64, dp, u64], ctypes.c_int),
         "qs_plan_validate": ([vp, vp, u64], ctypes.c_int),
+        "qs_insular_x_rewrite": ([i32, vp, u64, vp, u64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "qs_plan_kernel_source": ([vp, u64, ctypes.c_char_p, u64], i64),
         "qs_plan_kernel_program": ([vp, u64, ctypes.POINTER(ctypes.c_uint32), u64, ip], i64),
         "qs_state_create": ([i32, vp, ctypes.POINTER(vp)], ctypes.c_int),
@@ -438,6 +442,19 @@ def qs_apply_fused_static(state_ptr: int, n: int, targets, u: np.ndarray, precis
     check(_lib.qs_apply_fused_static(state_ptr, n, t, len(targets),
                                      uu.view(np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                      precision, _stream_ptr(stream)), "qs_apply_fused_static")
+
+
+def qs_insular_x_rewrite(n: int, gates) -> np.ndarray:
+    """The Pauli-frame rewrite an insular-X plan executes (gate array)."""
+    g = _gates_array(gates)
+    cnt = ctypes.c_uint64()
+    check(_lib.qs_insular_x_rewrite(int(n), g.ctypes.data_as(ctypes.c_void_p), len(g), None, 0,
+                                    ctypes.byref(cnt)), "qs_insular_x_rewrite")
+    out = np.zeros(cnt.value, dtype=g.dtype)
+    check(_lib.qs_insular_x_rewrite(int(n), g.ctypes.data_as(ctypes.c_void_p), len(g),
+                                    out.ctypes.data_as(ctypes.c_void_p), len(out), ctypes.byref(cnt)),
+          "qs_insular_x_rewrite")
+    return out
 
 
 def qs_sync(stream=None):

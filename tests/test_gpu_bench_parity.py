@@ -44,13 +44,16 @@ def _reference(workload):
 
 
 def _plan(Q, gates, which, n=N):
+    # "-x": planned as the Pauli-frame rewrite (insular X), as the bench does
+    ix = 1 if which.endswith("-x") else 0
+    which = which[:-2] if ix else which
     if which == "A":  # analytic-cost Kernelize, shared-memory kernels, FP32
-        return Q.Plan(n, gates, algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=SHM_MAX)
+        return Q.Plan(n, gates, algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=SHM_MAX, insular_x=ix)
     if which == "B":  # learned-cost Kernelize, fused kernels in 3xTF32
         from paper_2408_09055_gb300 import costmodel as CM
         net, _ = CM.load()
         opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3,
-                              shm_max_active=SHM_MAX, fuse_kmax=6, mlp=net)
+                              shm_max_active=SHM_MAX, fuse_kmax=6, mlp=net, insular_x=ix)
         plan = Q.Plan(n, gates, opts)
         plan._net = net
         return plan
@@ -61,7 +64,7 @@ def _plan(Q, gates, which, n=N):
     return Q.Plan(n, gates, algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=6, fuse_kmin=6, precision=prec, cost=cost)
 
 
-@pytest.mark.parametrize("which", ["A", "B", "F-TF32X3"])
+@pytest.mark.parametrize("which", ["A", "B", "F-TF32X3", "A-x", "B-x"])
 @pytest.mark.parametrize("workload", ["mixed", "entangling"])
 def test_bench_plans_match_oracle_elementwise_at_26_qubits(workload, which):
     need_gpu()

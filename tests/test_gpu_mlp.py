@@ -56,7 +56,8 @@ def test_expectile_gradient_matches_oracle():
     net.set_expectile(tau)
     theta = net.get_params().astype(np.float64)
     x, t = _data(257, 11)
-    loss, g = net.gradient(_dev(x).data_ptr(), _dev(t).data_ptr(), len(t))
+    xd, td = _dev(x), _dev(t)  # kept alive through the call
+    loss, g = net.gradient(xd.data_ptr(), td.data_ptr(), len(t))
     ref_loss, ref_g = OM.gradient(theta, x.astype(np.float64), t.astype(np.float64), F, H, tau=tau)
     assert abs(loss - ref_loss) <= 1e-4 * max(1.0, ref_loss)
     np.testing.assert_allclose(g, ref_g, rtol=1e-3, atol=1e-5 * float(np.max(np.abs(ref_g))))

@@ -225,7 +225,7 @@ def test_insular_x_stages_match_oracle(case, nbuf):
     else:
         n, L = 19, 14
         g = C.mixed_circuit(n, 900, 11)
-    plan = Q.Plan(n, g, local_qubits=L, insular_x=1, shm_max_active=12)
+    plan = Q.Plan(n, g, local_qubits=L, insular_x=Q.QS_INSULAR_X_STAGED, shm_max_active=12)
     frames = [plan.stage_frame(i)[0] for i in range(plan.stats().num_stages)]
     assert any(frames)
     psi0 = random_state(n, 3 + (nbuf or 0))
@@ -238,7 +238,7 @@ def test_insular_x_stages_need_two_chunk_buffers():
     from paper_2408_09055_gb300 import qsim as Q
     n, L = 17, 12
     g = _insular_x_rule_circuit(n, L, 0)
-    plan = Q.Plan(n, g, local_qubits=L, insular_x=1, shm_max_active=12)
+    plan = Q.Plan(n, g, local_qubits=L, insular_x=Q.QS_INSULAR_X_STAGED, shm_max_active=12)
     with pytest.raises(Q.QsError) as ei:
         run_host(plan, n, None, 1)
     assert ei.value.status == Q.QS_EINVAL
