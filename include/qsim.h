@@ -321,8 +321,9 @@ int qs_debug_tc_stall(int64_t limit_us);
  * far in this process, per load path: out[0] register gathers (32-bit
  * offsets), out[1] bulk row copies (cp.async.bulk; chosen when a tile's 64
  * columns are the 64 lowest qubits and five or more targets are at qubit
- * 18 or above), out[2] register gathers with 64-bit offsets (n > 32).
- * Writes min(cap, 3) entries; returns 3 (the number of paths) or QS_EINVAL. */
+ * 18 or above), out[2] register gathers with 64-bit offsets (n > 32),
+ * out[3] cp.async copies into a raw ring.  Writes min(cap, 4) entries;
+ * returns 4 (the number of paths) or QS_EINVAL.                             */
 int32_t qs_debug_tc_launch_counts(uint64_t* out, int32_t cap);
 
 /* Alg. 1's Execute with the state in host memory: for each stage, for each

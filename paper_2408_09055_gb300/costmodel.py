@@ -144,12 +144,15 @@ def _time_specs(n, specs, reps, st, s, threads, log=None):
 
 
 def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC_TF32X3, reps=3,
-           epochs=300, threads=None, log=print, weight=4, entangling_share=0.67, tau=0.5):
+           epochs=300, threads=None, log=print, weight=4, entangling_share=0.67, tau=0.5, ensemble=1,
+           contrast=False, shm_max=12):
     """Active refinement: plan freshly seeded workload circuits with the
     learned cost (Kernelize, fused kernels in `precision`), time exactly the
     kernels those plans chose, add them to the data and retrain.  A planner
     that minimises a learned cost steers towards kernels the model
-    underestimates; timing its own choices corrects those regions."""
+    underestimates; timing its own choices corrects those regions.  With
+    `contrast` the analytic plans' kernels of the same circuits are timed too,
+    so the model also learns the alternative it is weighed against."""
     import torch
     from synth import circuits as C
     threads = threads or os.cpu_count() or 4
@@ -171,15 +174,19 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
             wseed = 20_000 + int(rng.integers(0, 1 << 30))
             ent = rng.uniform() < entangling_share
             g = C.entangling_circuit(n, 10, wseed) if ent else C.mixed_circuit(n, 1200, wseed)
-            plan = Q.Plan(n, g, Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=precision, fuse_kmax=6,
-                                               mlp=net, shm_variant=2))
-            for k in range(plan.stats().num_kernels):
-                sub = g[plan.kernel_gates(k)]
-                if plan.kernel(k).type == Q.QS_KERNEL_FUSED:
-                    opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=6, precision=precision, cost=fcost)
-                else:
-                    opts = Q.default_opts(algo=Q.QS_ALGO_GREEDY, fuse_kmax=0, shm_max_active=14)
-                specs.append((sub, opts, opts.cost))
+            plans = [Q.Plan(n, g, Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=precision, fuse_kmax=6,
+                                                 mlp=net, shm_variant=2, shm_max_active=shm_max))]
+            if contrast:
+                plans.append(Q.Plan(n, g, Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=precision,
+                                                         fuse_kmax=6, shm_variant=2, shm_max_active=shm_max)))
+            for plan in plans:
+                for k in range(plan.stats().num_kernels):
+                    sub = g[plan.kernel_gates(k)]
+                    if plan.kernel(k).type == Q.QS_KERNEL_FUSED:
+                        opts = Q.default_opts(algo=Q.QS_ALGO_ORDERED, fuse_kmax=6, precision=precision, cost=fcost)
+                    else:
+                        opts = Q.default_opts(algo=Q.QS_ALGO_GREEDY, fuse_kmax=0, shm_max_active=14)
+                    specs.append((sub, opts, opts.cost))
         Xn, yn, kinds = _time_specs(n, specs, reps, st, s, threads)
         Xn = np.asarray(Xn, dtype=np.float32)
         yn = np.asarray(yn, dtype=np.float32)
@@ -192,8 +199,12 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
         parts = [np.concatenate(p) for p in (
             [X[base[0]]] + [Xr[rtr]] * weight, [y[base[0]]] + [yr[rtr]] * weight,
             [X[base[1]], Xr[rva]], [y[base[1]], yr[rva]], [X[base[2]], Xr[rte]], [y[base[2]], yr[rte]])]
-        net, metrics = train_parts((parts[0], parts[1]), (parts[2], parts[3]), (parts[4], parts[5]),
-                                   epochs=epochs, seed=seed, tau=tau)
+        if ensemble > 1:
+            net, metrics = train_ensemble((parts[0], parts[1]), (parts[2], parts[3]), (parts[4], parts[5]),
+                                          k=ensemble, seed=seed, tau=tau, epochs=epochs)
+        else:
+            net, metrics = train_parts((parts[0], parts[1]), (parts[2], parts[3]), (parts[4], parts[5]),
+                                       epochs=epochs, seed=seed, tau=tau)
         history.append({"kernels": int(len(yn)), "fused": int(sum(kinds)), "pred_over_actual": bias})
         if log:
             log(f"refinement round {r + 1}: +{len(yn)} kernels ({sum(kinds)} fused), "
@@ -205,11 +216,12 @@ def refine(net, X, y, n=N_REF, rounds=2, circuits=6, seed=0, precision=Q.QS_PREC
     return net, np.concatenate([X, Xr]), np.concatenate([y, yr]), metrics, test_idx
 
 
-def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, stream=None, log=None):
+def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, stream=None, log=None,
+              workload="mixed"):
     """The learned model's plan-level gain: for each seed, the mixed circuit
     (5000 gates) planned by Kernelize with the analytic table and with the
     learned cost under the same options (|A| <= shm_max, fused 3xTF32
-    kernels allowed, insular X), each plan timed on a resident n-qubit state (the
+    kernels allowed), each plan timed on a resident n-qubit state (the
     median of `reps` runs after one warm-up).  Returns per-seed circuit
     times and kernel counts and the gain sum(analytic) / sum(learned)."""
     import torch
@@ -217,7 +229,7 @@ def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, 
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
     st = Q.State(n, buf.data_ptr())
-    out = {"n": n, "gates": gates, "shm_max_active": shm_max, "seeds": [], "analytic_ms": [], "learned_ms": [],
+    out = {"n": n, "workload": workload, "shm_max_active": shm_max, "seeds": [], "analytic_ms": [], "learned_ms": [],
            "analytic_kernels": [], "learned_kernels": [], "learned_fused": []}
 
     def timed(plan):
@@ -230,9 +242,8 @@ def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, 
         return float(np.sum(ms)) / runs
 
     for seed in seeds:
-        g = C.mixed_circuit(n, gates, seed)
-        base = dict(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3, fuse_kmax=6, shm_max_active=shm_max,
-                    insular_x=1)
+        g = C.mixed_circuit(n, gates, seed) if workload == "mixed" else C.entangling_circuit(n, 40, seed)
+        base = dict(algo=Q.QS_ALGO_KERNELIZE, precision=Q.QS_PREC_TF32X3, fuse_kmax=6, shm_max_active=shm_max)
         pa = Q.Plan(n, g, Q.default_opts(**base))
         pl = Q.Plan(n, g, Q.default_opts(mlp=net, **base))
         out["seeds"].append(int(seed))
@@ -247,6 +258,50 @@ def plan_gain(net, seeds=range(101, 110), n=26, gates=5000, shm_max=12, reps=3, 
                 f"{out['learned_fused'][-1]} fused)")
     out["gain"] = float(np.sum(out["analytic_ms"]) / np.sum(out["learned_ms"]))
     return out
+
+
+def _unpack(theta, F, H):
+    o = 0
+    out = {}
+    for name, shape in (("W1", (F, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H,)), ("b3", (1,))):
+        size = int(np.prod(shape))
+        out[name] = np.asarray(theta[o:o + size], dtype=np.float64).reshape(shape)
+        o += size
+    return out
+
+
+def merge_ensemble(nets):
+    """One network whose output is the mean of the given networks' outputs
+    (same features F and width H each): their first layers side by side
+    (F x kH), the second weight matrix block-diagonal (ReLU acts element by
+    element, so the blocks never mix), the output weights divided by k and
+    the output biases averaged."""
+    F, H, k = nets[0].features, nets[0].hidden, len(nets)
+    ps = [_unpack(n.get_params(), F, H) for n in nets]
+    W1 = np.concatenate([p["W1"] for p in ps], axis=1)
+    b1 = np.concatenate([p["b1"] for p in ps])
+    W2 = np.zeros((k * H, k * H))
+    for i, p in enumerate(ps):
+        W2[i * H:(i + 1) * H, i * H:(i + 1) * H] = p["W2"]
+    b2 = np.concatenate([p["b2"] for p in ps])
+    W3 = np.concatenate([p["W3"] for p in ps]) / k
+    b3 = np.array([np.mean([p["b3"][0] for p in ps])])
+    net = Q.Mlp(F, k * H)
+    net.set_params(np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3, b3]).astype(np.float32))
+    return net
+
+
+def train_ensemble(train_set, val_set, test_set, k=4, seed=0, tau=0.5, **kw):
+    """k networks (seeds seed..seed+k-1) on the same parts, merged into one
+    whose prediction is their mean; metrics of the merged network."""
+    import torch
+    nets = [train_parts(train_set, val_set, test_set, seed=seed + i, tau=tau, **kw)[0] for i in range(k)]
+    net = merge_ensemble(nets)
+    s = torch.cuda.current_stream().cuda_stream
+    metrics = {name: evaluate(net, part[0], part[1], stream=s, tau=tau) for name, part in
+               (("train", train_set), ("validation", val_set), ("test", test_set))}
+    metrics["ensemble"] = k
+    return net, metrics
 
 
 def split(count, seed=0, fractions=(0.8, 0.1, 0.1)):
@@ -355,22 +410,32 @@ def main(argv=None):
     ap.add_argument("--data", default=None, help="reuse timed kernels saved by an earlier run")
     ap.add_argument("--tau", type=float, default=0.5,
                     help="expectile of ln(time) the network learns (0.5: mean squared error)")
+    ap.add_argument("--ensemble", type=int, default=1, help="networks averaged into the saved one")
+    ap.add_argument("--contrast", action="store_true",
+                    help="refinement also times the analytic plans' kernels of the same circuits")
     a = ap.parse_args(argv)
     if a.data:
         d = np.load(a.data)
         X, y, meta = d["X"], d["y"], json.loads(str(d["meta"]))
     else:
         X, y, meta = generate(count=a.count, seed=a.seed)
-    net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print, tau=a.tau)
+    if a.ensemble > 1:
+        tr, va, te = split(len(y), a.seed)
+        net, metrics = train_ensemble((X[tr], y[tr]), (X[va], y[va]), (X[te], y[te]), k=a.ensemble, seed=a.seed,
+                                      tau=a.tau, epochs=a.epochs)
+    else:
+        net, metrics = train(X, y, epochs=a.epochs, seed=a.seed, log=print, tau=a.tau)
     test_idx = split(len(y), a.seed)[2]
     if a.refine_rounds:
         net, X, y, metrics, test_idx = refine(net, X, y, rounds=a.refine_rounds, seed=a.seed, epochs=a.epochs,
-                                              tau=a.tau)
+                                              tau=a.tau, ensemble=a.ensemble, contrast=a.contrast)
         meta["refine_rounds"] = a.refine_rounds
         meta["count"] = int(len(y))
     np.savez(os.path.splitext(a.out)[0] + "_data.npz", X=X, y=y, test_idx=test_idx, meta=json.dumps(meta))
     meta["metrics"] = metrics
     meta["tau"] = a.tau
+    meta["ensemble"] = a.ensemble
+    meta["contrast"] = bool(a.contrast)
     save(net, a.out, meta)
     print(json.dumps(meta))
 

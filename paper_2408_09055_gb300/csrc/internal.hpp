@@ -266,8 +266,9 @@ void tc_prepare_weights_into(const float* u, bool x3, float* out);  // tc_weight
 int tc_check_error(cudaStream_t s, bool clear);
 void tc_set_stall(uint64_t ns);  // test-only fault injection (qs_debug_tc_stall)
 // tensor-core load paths: register gathers with 32-bit offsets, bulk row
-// copies (rows in many 2 MiB pages), register gathers with 64-bit offsets
-enum TcVariant { kTcRegister = 0, kTcBulk = 1, kTcWide = 2, kTcVariants = 3 };
+// copies (rows in many 2 MiB pages), register gathers with 64-bit offsets,
+// cp.async into a raw ring
+enum TcVariant { kTcRegister = 0, kTcBulk = 1, kTcWide = 2, kTcCpAsync = 3, kTcVariants = 4 };
 void tc_launch_counts(uint64_t* out, int cap);
 // U (2^k x 2^k, row-major complex64) widened to 2^kw x 2^kw as U (x) I on
 // kw - k added index bits above bit k-1; out: 2 * 4^kw floats.

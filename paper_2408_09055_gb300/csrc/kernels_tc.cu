@@ -21,6 +21,7 @@
 // is freed and the CTA returns).
 #include <atomic>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -187,7 +188,7 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
-template <int CB, bool X3, int ST, bool WIDE, bool BULK, int RS>
+template <int CB, bool X3, int ST, bool WIDE, bool BULK, int RS, bool CPA = false>
 __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __grid_constant__ TcParams P) {
   using Off = typename std::conditional<WIDE, uint64_t, uint32_t>::type;  // amplitude offsets
   constexpr int RAW_PITCH = (1 << CB) + 8;      // float2 per raw row (64 B of padding)
@@ -318,7 +319,65 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
     atomicExch(&g_tc_error, 1);
   };
 
-  if (BULK && warp < kProdWarps) {
+  if (CPA && warp < kProdWarps) {
+    // ---- producers with cp.async: each thread copies its own elements of
+    // the tiles RS - 1 ahead into its private slots of a raw ring (slot r,
+    // element e at r * EPT * 256 + e * 256 + tid), waits for its own oldest
+    // group, rounds and stores the operand.  No register holds data in
+    // flight and no other thread reads a thread's slots.
+    float2* const raw = reinterpret_cast<float2*>(smem + ST * NOP * B_FLOATS);
+    const uint32_t raw_s = smem_u32(raw + tid);
+    Off goff[EPT];
+    uint32_t soff[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const int task = warp + kProdWarps * e;
+      const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
+      goff[e] = (Off)(rowoff[j] | coloff[c]);
+      soff[e] = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
+    }
+    const uint64_t g = gridDim.x;
+    auto issue = [&](uint64_t bt, uint32_t slot) {
+      if (bt < nb) {
+        const float2* src = P.psi + tile_base(bt);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const uint32_t dst = raw_s + (slot * (uint32_t)(EPT * 256) + (uint32_t)(e * 256)) * 8u;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
+                       "l"(__cvta_generic_to_global(src + goff[e]))
+                       : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int k = 0; k < RS - 1; ++k) issue(blockIdx.x + (uint64_t)k * g, (uint32_t)k);
+    uint32_t it = 0;
+    for (uint64_t bt = blockIdx.x; bt < nb; bt += g, ++it) {
+      issue(bt + (uint64_t)(RS - 1) * g, (it + RS - 1) % RS);  // the slot tile it - 1 used
+      asm volatile("cp.async.wait_group %0;" ::"n"(RS - 1) : "memory");  // this thread's tile `it`
+      const float2* mine = raw + (it % RS) * (uint32_t)(EPT * 256) + tid;
+      float2 v[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[e] = mine[e * 256];
+      const uint32_t s2 = it % ST, ph = (it / ST) & 1u;
+      const bool ok = mbar_wait_or_abort(smem_u32(&bar_empty[s2]), ph ^ 1u, &abort_all);
+      if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together
+        fail();
+        break;
+      }
+      float* bh = Bop + s2 * NOP * B_FLOATS;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const float hr = tf32_rna(v[e].x), hi = tf32_rna(v[e].y);
+        *reinterpret_cast<float2*>(bh + soff[e]) = make_float2(hr, hi);
+        if (X3) *reinterpret_cast<float2*>(bh + B_FLOATS + soff[e]) = make_float2(v[e].x - hr, v[e].y - hi);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_full[s2]));
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing in flight when the thread leaves
+  } else if (BULK && warp < kProdWarps) {
     // ---- producers reading the raw ring ----
     uint32_t roff[EPT], soff[EPT];
 #pragma unroll
@@ -386,7 +445,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
           if (done || global_ns() - t0 > kWaitNs) break;
         }
       }
-  } else if (!BULK && warp < kProdWarps) {
+  } else if (!BULK && !CPA && warp < kProdWarps) {
     // ---- producers ----
     // two register buffers alternate, so the loads of the tile after next
     // are in flight while this tile is rounded and stored
@@ -563,30 +622,32 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
                  : "memory");
 }
 
-template <int CB, bool X3, int ST, bool BULK, int RS>
+template <int CB, bool X3, int ST, bool BULK, int RS, bool CPA = false>
 constexpr size_t tc_smem() {
   constexpr size_t N = size_t(1) << CB;
-  // the operand ring (the unitary lives in TMEM), plus the raw ring with BULK
-  return (X3 ? 2 : 1) * ST * N * kTcKR * 4 + (BULK ? RS * size_t(kTcDim) * (N + 8) * 8 : 0);
+  // the operand ring (the unitary lives in TMEM), plus the raw ring with
+  // BULK (padded rows) or CPA (a tile per slot)
+  return (X3 ? 2 : 1) * ST * N * kTcKR * 4 + (BULK ? RS * size_t(kTcDim) * (N + 8) * 8 : 0) +
+         (CPA ? RS * size_t(kTcDim) * N * 8 : 0);
 }
 
-template <int CB, bool X3, int ST, bool WIDE, bool BULK = false, int RS = 1>
+template <int CB, bool X3, int ST, bool WIDE, bool BULK = false, int RS = 1, bool CPA = false>
 int launch_tc(const TcParams& P, cudaStream_t s) {
   static std::atomic<unsigned> attr_done{0};  // one bit per device ordinal < 32
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  constexpr size_t smem = tc_smem<CB, X3, ST, BULK, RS>();
+  constexpr size_t smem = tc_smem<CB, X3, ST, BULK, RS, CPA>();
   static_assert(smem <= 227u * 1024u - 2048u, "tensor-core pipeline exceeds shared memory");
   if (dev >= 32 || !((attr_done.load() >> dev) & 1u)) {
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS>,
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS, CPA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 32) attr_done.fetch_or(1u << dev);
   }
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms);
-  fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS><<<(unsigned)grid, kTcThreads2 + (BULK ? 32 : 0), smem, s>>>(P);
+  fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS, CPA><<<(unsigned)grid, kTcThreads2 + (BULK ? 32 : 0), smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error("tensor-core fused kernel launch", e);
@@ -661,6 +722,21 @@ int tc_check_error(cudaStream_t s, bool clear) {
   return v ? QS_ETIMEDOUT : QS_OK;
 }
 
+// Load form of the tiles away from the bulk and 64-bit cases: register
+// gathers (default), or cp.async into a raw ring (QSIM_TC_LOAD=cpasync).
+// Measured at 30 qubits, every kernel of the 40-layer entangling circuit
+// fused: register gathers 3.48 ms (TF32) / 3.87 ms (3xTF32) per launch,
+// cp.async 4.53 / 4.78 ms.
+static bool tc_cp_async() {
+  static const int v = [] {
+    const char* e = std::getenv("QSIM_TC_LOAD");
+    if (e && std::strcmp(e, "cpasync") == 0) return 1;
+    if (e && std::strcmp(e, "register") == 0) return 0;
+    return 0;
+  }();
+  return v != 0;
+}
+
 // a.u points at the prepared weights (tc_prepare_weights) in device memory
 int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
   if (a.k != kTcK) return QS_EUNSUPPORTED;
@@ -702,6 +778,12 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
   } else if (P.contig && cb == 6 && high >= 5) {
     v = kTcBulk;
     rc = x3 ? launch_tc<6, true, 2, false, true, 2>(P, s) : launch_tc<6, false, 3, false, true, 3>(P, s);
+  } else if (tc_cp_async()) {
+    v = kTcCpAsync;
+    if (x3)
+      rc = cb == 5 ? launch_tc<5, true, 2, false, false, 3, true>(P, s) : launch_tc<6, true, 2, false, false, 3, true>(P, s);
+    else
+      rc = cb == 5 ? launch_tc<5, false, 4, false, false, 3, true>(P, s) : launch_tc<6, false, 4, false, false, 3, true>(P, s);
   } else {
     v = kTcRegister;
     if (x3) rc = cb == 5 ? launch_tc<5, true, 3, false>(P, s) : launch_tc<6, true, 3, false>(P, s);

@@ -471,11 +471,11 @@ def qs_debug_tc_stall(limit_us: int):
 
 def qs_debug_tc_launch_counts() -> dict:
     """Tensor-core fused launches so far, per load path (test-only)."""
-    out = (ctypes.c_uint64 * 3)()
-    nv = _lib.qs_debug_tc_launch_counts(out, 3)
+    out = (ctypes.c_uint64 * 4)()
+    nv = _lib.qs_debug_tc_launch_counts(out, 4)
     if nv < 0:
         check(nv, "qs_debug_tc_launch_counts")
-    return {"register": int(out[0]), "bulk": int(out[1]), "wide": int(out[2])}
+    return {"register": int(out[0]), "bulk": int(out[1]), "wide": int(out[2]), "cpasync": int(out[3])}
 
 
 def _fp(a: np.ndarray):

@@ -65,6 +65,25 @@ def test_expectile_gradient_matches_oracle():
         net.set_expectile(1.0)
 
 
+def test_merged_ensemble_is_the_mean_of_its_networks():
+    # the block-diagonal merge is exact: its FP32 forward equals the mean of
+    # the member networks' forwards
+    need_gpu()
+    from paper_2408_09055_gb300 import costmodel as CM
+    from paper_2408_09055_gb300 import qsim as Q
+    nets = [Q.Mlp(F, 32, seed=s) for s in (1, 2, 3)]
+    merged = CM.merge_ensemble(nets)
+    x, _ = _data(200, 13)
+    xd = _dev(x)
+    ys = []
+    for net in nets + [merged]:
+        y = torch.empty(200, dtype=torch.float32, device="cuda")
+        net.forward(xd.data_ptr(), 200, y.data_ptr(), bf16=False)
+        ys.append(y.cpu().numpy().astype(np.float64))
+    mean = np.mean(ys[:3], axis=0)
+    assert np.max(np.abs(ys[3] - mean)) <= 1e-5 * max(1.0, float(np.max(np.abs(mean))))
+
+
 def _bf16(a):
     """Round-to-nearest-even to bfloat16, kept in float64."""
     u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
