@@ -17,6 +17,10 @@ from tests.gpu_util import need_gpu
 
 pytestmark = pytest.mark.gpu
 
+# the learned plan may be this much slower than the analytic plan on the
+# held-out seeds (measured gains are recorded in the design doc)
+GAIN_FLOOR = 0.99
+
 
 def _analytic_design(X):
     fused = X[:, 41] > 0.5
@@ -47,3 +51,19 @@ def test_learned_cost_beats_the_analytic_cost_on_held_out_kernels():
     assert e_learned < 0.12, e_learned
     assert e_learned < 0.9 * e_fitted, (e_learned, e_fitted)
     assert e_learned < 0.5 * e_table, (e_learned, e_table)
+
+
+def test_learned_plan_against_analytic_plan_on_held_out_seeds():
+    # the plan-level comparison of the cost model (config 3's evaluation at
+    # 26 qubits): held-out seeds 101-109 of the 5000-gate mixed circuit, Kernelize
+    # with the analytic table and with the committed network under the same
+    # options, each plan timed on the GPU.  The measured gain is reported;
+    # the learned plan must stay within GAIN_FLOOR of the analytic one.
+    need_gpu()
+    from paper_2408_09055_gb300 import costmodel as CM
+    net, meta = CM.load()
+    r = CM.plan_gain(net, seeds=range(101, 110), n=26, reps=3)
+    print(f"learned-plan gain over the analytic plan: {r['gain']:.4f} "
+          f"(analytic {r['analytic_ms']}, learned {r['learned_ms']})")
+    assert all(k > 0 for k in r["learned_kernels"])
+    assert r["gain"] >= GAIN_FLOOR, r
