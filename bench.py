@@ -296,6 +296,76 @@ def profile_run(args):
     return 0
 
 
+def config2_measure(args):
+    """The dense entangling circuit (40 layers: U3 on every qubit, CP + RXX on
+    a random matching, seed 100) on a resident n-qubit state with every
+    kernel fused into a dense 2^k unitary, k = 5, 6, 7 forced in turn, in
+    FP32 on CUDA cores, TF32 and 3xTF32 on the tensor cores (k = 5 widened
+    to the tensor-core kernel's 6 targets; no tensor-core form for k = 7),
+    beside plan A.  Per form: ms per circuit, kernels, average launch time
+    and its HBM fraction; error against the FP64 oracle of the same
+    generator at `err_n` qubits (rank 0)."""
+    import numpy as np
+    import torch
+    from paper_2408_09055_gb300 import qsim as Q
+    from oracle import sim
+    n, err_n = args.config2, 26
+    hbm, _, src = peaks()
+    buf = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    st = Q.State(n, buf.data_ptr())
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    eg = workload_gates("entangling", n)
+    small = workload_gates("entangling", err_n)
+    ref = sim.apply(err_n, small)
+    ebuf = torch.empty(2 << err_n, dtype=torch.float32, device="cuda")
+    est = Q.State(err_n, ebuf.data_ptr())
+    names = {Q.QS_PREC_FP32: "FP32 CUDA cores", Q.QS_PREC_TF32: "TF32", Q.QS_PREC_TF32X3: "3xTF32"}
+
+    def fused_opts(k, prec):
+        cost = Q.default_cost_table()
+        for j in range(16):
+            cost.fuse_cost[j] = 1.0
+        return Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, precision=prec, fuse_kmax=k, fuse_kmin=k, cost=cost)
+
+    rows = []
+    forms = [("A", None, None)] + [(f"F{k}", k, p) for k in (5, 6, 7)
+                                   for p in (Q.QS_PREC_FP32, Q.QS_PREC_TF32, Q.QS_PREC_TF32X3)]
+    for label, k, prec in forms:
+        row = {"form": label if k is None else f"fused k={k}, {names[prec]}"}
+        try:
+            if k is None:
+                opts = Q.default_opts(algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=args.shm_max)
+            else:
+                opts = fused_opts(k, prec)
+            plan = Q.Plan(n, eg, opts)
+        except Q.QsError as e:
+            row["unsupported"] = str(e)
+            rows.append(row)
+            continue
+        ps = plan.stats()
+        st.set_zero(sp)
+        ms, pk, runs = time_plan(Q, torch, st, plan, args.steps, args.warmup, stream, 1)
+        types = by_kernel_type(Q, plan, pk, runs, n, hbm)
+        row.update({"ms_per_circuit": ms / args.steps, "kernels": int(ps.num_kernels),
+                    "fused_kernels": int(ps.num_fused), "kernel_types": types,
+                    "norm2_after": st.norm2(sp)})
+        eplan = Q.Plan(err_n, small, opts)
+        est.set_zero(sp)
+        est.run(eplan, sp)
+        got = est.read(stream=sp).astype(np.complex128)
+        fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
+        row["error_vs_fp64"] = {"n_qubits": err_n, "one_minus_fidelity": float(1 - fid),
+                                "max_abs": float(np.max(np.abs(ref - got)))}
+        rows.append(row)
+        del plan, eplan
+    line = {"metric": "entangling circuit, every kernel fused (config 2)", "n_qubits": n,
+            "workload": entangling_desc(n), "gates": int(len(eg)), "steps": args.steps, "warmup": args.warmup,
+            "unit": "ms/circuit", "peak_hbm_gbs": hbm, "peak_source": src, "forms": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _copy_peaks(torch, host, dev, nbytes, reps=3):
     """Page-locked host <-> HBM copy bandwidth (GB/s): each direction alone,
     and both at once on two streams (their sum) -- the staged loop's bound."""
@@ -558,7 +628,12 @@ def main():
     ap.add_argument("--remap", type=int, default=0, metavar="N",
                     help="measure the qubit-remap kernel on an N-qubit state instead")
     ap.add_argument("--chunk-buffers", type=int, default=4, choices=[1, 2, 3, 4])
+    ap.add_argument("--config2", type=int, default=0, metavar="N",
+                    help="the entangling circuit on a resident N-qubit state with every kernel fused "
+                         "(k = 5, 6, 7; FP32 / TF32 / 3xTF32) beside plan A, errors against FP64 at 26 qubits")
     args = ap.parse_args()
+    if args.config2:
+        return config2_measure(args)
     if args.remap:
         return remap_measure(args)
     if args.staged:
