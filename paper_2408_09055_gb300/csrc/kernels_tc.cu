@@ -175,7 +175,6 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parit
 //                holds data in flight.
 constexpr int kProdWarps = 8;
 constexpr int kDrainWarps = 4;
-constexpr int kTcThreads2 = 32 * (kProdWarps + kDrainWarps + 1);  // + one loader warp with BULK
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
@@ -188,8 +187,9 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
-template <int CB, bool X3, int ST, bool WIDE, bool BULK, int RS, bool CPA = false>
-__global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __grid_constant__ TcParams P) {
+template <int CB, bool X3, int ST, bool WIDE, bool BULK, int RS, bool CPA = false, int PW = kProdWarps, int NB = 2>
+__global__ void __launch_bounds__(32 * (PW + kDrainWarps + 1) + 32, 1)
+    fused_tc_kernel(const __grid_constant__ TcParams P) {
   using Off = typename std::conditional<WIDE, uint64_t, uint32_t>::type;  // amplitude offsets
   constexpr int RAW_PITCH = (1 << CB) + 8;      // float2 per raw row (64 B of padding)
   constexpr int RAW_STAGE = kTcDim * RAW_PITCH;  // float2 per raw stage
@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
   constexpr uint32_t A_FLOATS = kTcKR * kTcKR;
   constexpr uint32_t B_FLOATS = N * kTcKR;
   constexpr int TASKS = (N / 8) * (kTcDim / 4);  // warp accesses per tile: 8 columns x 4 rows
-  constexpr int EPT = TASKS / kProdWarps;        // per producer thread
+  static_assert(TASKS % PW == 0 && NB >= 2, "producer split");
+  constexpr int EPT = TASKS / PW;                // per producer thread
   // tensor memory: A (hi, then lo) in columns [0, 128*NOP), two accumulators after it
   constexpr uint32_t ACC0 = kTcKR * NOP;
   constexpr uint32_t TMEM_COLS = (ACC0 + 2 * N) <= 256 ? 256 : 512;
@@ -234,13 +235,13 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
     }
     nruns = nr;
   }
-  for (int r = tid; r < kTcDim; r += kTcThreads2) {
+  for (int r = tid; r < kTcDim; r += (int)blockDim.x) {
     unsigned long long o = 0;
     for (int j = 0; j < kTcK; ++j)
       if ((r >> j) & 1) o |= 1ull << P.targets[j];
     rowoff[r] = o;
   }
-  for (int c = tid; c < N; c += kTcThreads2) {
+  for (int c = tid; c < N; c += (int)blockDim.x) {
     unsigned long long o = 0;
     for (int j = 0; j < CB; ++j)
       if ((c >> j) & 1) o |= 1ull << P.cols[j];
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
   if (tid == 0) {
     for (int s = 0; s < ST; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[s])),
-                   "r"(32 * kProdWarps) : "memory");
+                   "r"(32 * PW) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[s])) : "memory");
     }
     for (int a = 0; a < 2; ++a) {
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
     for (int r = 0; r < RS; ++r) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_rfull[r])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_rempty[r])),
-                   "r"(32 * kProdWarps) : "memory");
+                   "r"(32 * PW) : "memory");
     }
     abort_all = 0;
   }
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
     atomicExch(&g_tc_error, 1);
   };
 
-  if (CPA && warp < kProdWarps) {
+  if (CPA && warp < PW) {
     // ---- producers with cp.async: each thread copies its own elements of
     // the tiles RS - 1 ahead into its private slots of a raw ring (slot r,
     // element e at r * EPT * 256 + e * 256 + tid), waits for its own oldest
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
     uint32_t soff[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      const int task = warp + kProdWarps * e;
+      const int task = warp + PW * e;
       const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
       goff[e] = (Off)(rowoff[j] | coloff[c]);
       soff[e] = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
@@ -377,12 +378,12 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
       mbar_arrive(smem_u32(&bar_full[s2]));
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // nothing in flight when the thread leaves
-  } else if (BULK && warp < kProdWarps) {
+  } else if (BULK && warp < PW) {
     // ---- producers reading the raw ring ----
     uint32_t roff[EPT], soff[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      const int task = warp + kProdWarps * e;
+      const int task = warp + PW * e;
       const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
       roff[e] = (uint32_t)(j * RAW_PITCH + c);
       soff[e] = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&bar_full[s]));
     }
-  } else if (BULK && warp == kProdWarps + kDrainWarps + 1) {
+  } else if (BULK && warp == PW + kDrainWarps + 1) {
     // ---- loader ----
     uint32_t it = 0;
     for (uint64_t bt = blockIdx.x; bt < nb; bt += gridDim.x, ++it) {
@@ -445,16 +446,16 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
           if (done || global_ns() - t0 > kWaitNs) break;
         }
       }
-  } else if (!BULK && !CPA && warp < kProdWarps) {
+  } else if (!BULK && !CPA && warp < PW) {
     // ---- producers ----
-    // two register buffers alternate, so the loads of the tile after next
-    // are in flight while this tile is rounded and stored
-    float2 va[EPT], vb[EPT];
+    // NB register buffers rotate: while one tile is rounded and stored, the
+    // loads of the next NB - 1 tiles are in flight
+    float2 vb[NB][EPT];
     Off goff[EPT];       // element offsets inside a tile (the same for every tile)
     uint32_t soff[EPT];  // and their operand positions (floats)
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      const int task = warp + kProdWarps * e;
+      const int task = warp + PW * e;
       const int c = 8 * (task % (N / 8)) + (lane & 7), j = 4 * (task / (N / 8)) + (lane >> 3);
       goff[e] = (Off)(rowoff[j] | coloff[c]);
       soff[e] = core_off((uint32_t)c, (uint32_t)(2 * j)) >> 2;
@@ -486,20 +487,29 @@ __global__ void __launch_bounds__(kTcThreads2 + 32, 1) fused_tc_kernel(const __g
     const uint64_t g = gridDim.x;
     uint64_t bt = blockIdx.x;
     uint32_t it = 0;
-    if (bt < nb) load(bt, va);
-    if (bt + g < nb) load(bt + g, vb);
-    while (bt < nb) {
-      if (!put(it, va)) break;
-      ++it;
-      bt += g;
-      if (bt + g < nb) load(bt + g, va);
-      if (bt >= nb) break;
-      if (!put(it, vb)) break;
-      ++it;
-      bt += g;
-      if (bt + g < nb) load(bt + g, vb);
+#pragma unroll
+    for (int k = 0; k < NB - 1; ++k)
+      if (bt + (uint64_t)k * g < nb) load(bt + (uint64_t)k * g, vb[k]);
+    bool go = bt < nb;
+    while (go) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        // tile bt is in vb[k]; the buffer of the tile before it is free
+        const uint64_t ahead = bt + (uint64_t)(NB - 1) * g;
+        if (ahead < nb) load(ahead, vb[(k + NB - 1) % NB]);
+        if (!put(it, vb[k])) {
+          go = false;
+          break;
+        }
+        ++it;
+        bt += g;
+        if (bt >= nb) {
+          go = false;
+          break;
+        }
+      }
     }
-  } else if (warp < kProdWarps + kDrainWarps) {
+  } else if (warp < PW + kDrainWarps) {
     // ---- drain ----
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     const int jrow = 16 * q + (lane >> 1);
@@ -631,7 +641,8 @@ constexpr size_t tc_smem() {
          (CPA ? RS * size_t(kTcDim) * N * 8 : 0);
 }
 
-template <int CB, bool X3, int ST, bool WIDE, bool BULK = false, int RS = 1, bool CPA = false>
+template <int CB, bool X3, int ST, bool WIDE, bool BULK = false, int RS = 1, bool CPA = false, int PW = kProdWarps,
+          int NB = 2>
 int launch_tc(const TcParams& P, cudaStream_t s) {
   static std::atomic<unsigned> attr_done{0};  // one bit per device ordinal < 32
   int dev = 0, sms = 148;
@@ -640,14 +651,15 @@ int launch_tc(const TcParams& P, cudaStream_t s) {
   constexpr size_t smem = tc_smem<CB, X3, ST, BULK, RS, CPA>();
   static_assert(smem <= 227u * 1024u - 2048u, "tensor-core pipeline exceeds shared memory");
   if (dev >= 32 || !((attr_done.load() >> dev) & 1u)) {
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS, CPA>,
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS, CPA, PW, NB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 32) attr_done.fetch_or(1u << dev);
   }
   const uint64_t nb = 1ull << (P.n - kTcK - CB);
   const uint64_t grid = std::min<uint64_t>(nb, (uint64_t)sms);
-  fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS, CPA><<<(unsigned)grid, kTcThreads2 + (BULK ? 32 : 0), smem, s>>>(P);
+  constexpr int threads = 32 * (PW + kDrainWarps + 1) + (BULK ? 32 : 0);
+  fused_tc_kernel<CB, X3, ST, WIDE, BULK, RS, CPA, PW, NB><<<(unsigned)grid, threads, smem, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error("tensor-core fused kernel launch", e);
@@ -723,18 +735,20 @@ int tc_check_error(cudaStream_t s, bool clear) {
 }
 
 // Load form of the tiles away from the bulk and 64-bit cases: register
-// gathers (default), or cp.async into a raw ring (QSIM_TC_LOAD=cpasync).
+// gathers by eight producer warps with two buffers (default), sixteen warps
+// with three buffers (QSIM_TC_LOAD=reg16), or cp.async into a raw ring
+// (QSIM_TC_LOAD=cpasync).
 // Measured at 30 qubits, every kernel of the 40-layer entangling circuit
 // fused: register gathers 3.48 ms (TF32) / 3.87 ms (3xTF32) per launch,
 // cp.async 4.53 / 4.78 ms.
-static bool tc_cp_async() {
+static int tc_load_form() {
   static const int v = [] {
     const char* e = std::getenv("QSIM_TC_LOAD");
     if (e && std::strcmp(e, "cpasync") == 0) return 1;
-    if (e && std::strcmp(e, "register") == 0) return 0;
+    if (e && std::strcmp(e, "reg16") == 0) return 2;
     return 0;
   }();
-  return v != 0;
+  return v;
 }
 
 // a.u points at the prepared weights (tc_prepare_weights) in device memory
@@ -778,7 +792,15 @@ int launch_fused_tc(const FusedLaunch& a, cudaStream_t s) {
   } else if (P.contig && cb == 6 && high >= 5) {
     v = kTcBulk;
     rc = x3 ? launch_tc<6, true, 2, false, true, 2>(P, s) : launch_tc<6, false, 3, false, true, 3>(P, s);
-  } else if (tc_cp_async()) {
+  } else if (tc_load_form() == 2) {  // sixteen producer warps, three register buffers
+    v = kTcRegister;
+    if (x3)
+      rc = cb == 5 ? launch_tc<5, true, 3, false, false, 1, false, 16, 3>(P, s)
+                   : launch_tc<6, true, 3, false, false, 1, false, 16, 3>(P, s);
+    else
+      rc = cb == 5 ? launch_tc<5, false, 6, false, false, 1, false, 16, 3>(P, s)
+                   : launch_tc<6, false, 6, false, false, 1, false, 16, 3>(P, s);
+  } else if (tc_load_form() == 1) {
     v = kTcCpAsync;
     if (x3)
       rc = cb == 5 ? launch_tc<5, true, 2, false, false, 3, true>(P, s) : launch_tc<6, true, 2, false, false, 3, true>(P, s);
