@@ -110,9 +110,7 @@ def test_every_conjugation_rule_reproduces_the_oracle(seed, fuse):
 @pytest.mark.parametrize("kind,n,L", [("mixed", 14, 12), ("mixed", 16, 12), ("mixed", 16, 13),
                                       ("layered", 15, 12)])
 def test_staged_mixed_circuits_with_insular_x(kind, n, L, mode):
-    g = (C.mixed_circuit(n, 400, 3 * n + L) if kind == "mixed"
-         else C.make_gates([(C.X, q, None, 0, 0, 0) for q in range(n)]) if False
-         else C.layered_u3_cz(n, 6, n + L))
+    g = C.mixed_circuit(n, 400, 3 * n + L) if kind == "mixed" else C.layered_u3_cz(n, 6, n + L)
     if kind == "layered":  # X layers between the U3/CZ layers
         extra = C.make_gates([(C.X, q, None, 0, 0, 0) for q in range(0, n, 2)])
         g = C.concat(g[: len(g) // 2], extra, g[len(g) // 2:], extra)
@@ -129,15 +127,12 @@ def test_staged_mixed_circuits_with_insular_x(kind, n, L, mode):
 def test_insular_x_never_needs_more_stages_on_mixed_circuits():
     # X no longer forces its qubit local, so a stage admits at least the
     # gates it did; on these circuits that saves stages or ties
-    fewer = 0
     for seed, (n, L) in enumerate([(20, 14), (22, 16), (24, 16), (24, 18)]):
         g = C.mixed_circuit(n, 1500, 40 + seed)
         a = Q.Plan(n, g, local_qubits=L, shm_max_active=12, fuse_kmax=0, shm_variant=2).stats().num_stages
         b = Q.Plan(n, g, local_qubits=L, shm_max_active=12, fuse_kmax=0, shm_variant=2,
                    insular_x=Q.QS_INSULAR_X_STAGED).stats().num_stages
         assert b <= a, (n, L, a, b)
-        fewer += b < a
-    assert fewer >= 0
 
 
 def test_frame_export_on_unstaged_and_bad_stage():
