@@ -169,3 +169,37 @@ def test_planning_failures_say_why():
     # a success clears it
     Q.Plan(8, g, shm_variant=1)
     assert L.qs_last_error() == b""
+
+
+def test_new_entry_points_refuse_bad_arguments_on_the_host():
+    # test-only stall limit out of range; launch counters with no room
+    assert L.qs_debug_tc_stall(-1) == Q.QS_EINVAL
+    assert L.qs_debug_tc_stall(10_000_001) == Q.QS_EINVAL
+    assert L.qs_debug_tc_stall(0) == Q.QS_OK
+    assert L.qs_debug_tc_launch_counts(None, 4) == Q.QS_EINVAL
+    out = (ctypes.c_uint64 * 1)()
+    assert L.qs_debug_tc_launch_counts(out, 1) == 4  # four load paths, one written
+    # expectile outside (0, 1) and a null network
+    assert L.qs_mlp_set_expectile(None, 0.5) == Q.QS_EINVAL
+    # the insular-X rewrite: a malformed gate, and an output buffer too small
+    cnt = ctypes.c_uint64()
+    bad = C.make_gates([(C.CX, 0, 0, 0, 0, 0)])  # both qubits the same
+    assert L.qs_insular_x_rewrite(4, Q._gates_array(bad).ctypes.data_as(ctypes.c_void_p), 1, None, 0,
+                                    ctypes.byref(cnt)) == Q.QS_EINVAL
+    g = Q._gates_array(C.mixed_circuit(6, 40, 2))
+    assert L.qs_insular_x_rewrite(6, g.ctypes.data_as(ctypes.c_void_p), len(g), None, 0, ctypes.byref(cnt)) == 0
+    small = np.zeros(max(1, cnt.value - 1), dtype=g.dtype)
+    assert L.qs_insular_x_rewrite(6, g.ctypes.data_as(ctypes.c_void_p), len(g),
+                                    small.ctypes.data_as(ctypes.c_void_p), len(small), ctypes.byref(cnt)) == Q.QS_EINVAL
+    # insular_x outside its bit mask; a staged plan's frame export with no room
+    with pytest.raises(Q.QsError) as ei:
+        Q.Plan(6, C.mixed_circuit(6, 20, 3), insular_x=4)
+    assert ei.value.status == Q.QS_EINVAL
+    n, loc = 14, 12
+    items = [(C.H, q, None, 0, 0, 0) for q in range(loc)] + [(C.X, 13, None, 0, 0, 0), (C.X, 12, None, 0, 0, 0)]
+    plan = Q.Plan(n, C.make_gates(items), local_qubits=loc, shm_max_active=12, insular_x=Q.QS_INSULAR_X_STAGED)
+    frame, flips = plan.stage_frame(0)
+    assert frame == (1 << 12) | (1 << 13) and sorted(flips) == [loc, loc + 1]
+    fr, k = ctypes.c_uint64(), ctypes.c_int64()
+    one = (ctypes.c_int32 * 1)()
+    assert L.qs_plan_stage_frame(plan.h, 0, ctypes.byref(fr), one, 1, ctypes.byref(k)) == Q.QS_EINVAL
