@@ -399,7 +399,8 @@ def load(path=MODEL_PATH):
 def main(argv=None):
     """python -m paper_2408_09055_gb300.costmodel [--count N] [--out PATH]:
     times `count` kernels on a 30-qubit state, trains, saves the model and the
-    dataset beside it."""
+    dataset beside it.  With --evaluate it loads the model at --out instead
+    and prints plan_gain's JSON for the given qubits, seeds and workload."""
     import argparse
     ap = argparse.ArgumentParser()
     ap.add_argument("--count", type=int, default=6144)
@@ -413,7 +414,18 @@ def main(argv=None):
     ap.add_argument("--ensemble", type=int, default=1, help="networks averaged into the saved one")
     ap.add_argument("--contrast", action="store_true",
                     help="refinement also times the analytic plans' kernels of the same circuits")
+    ap.add_argument("--evaluate", action="store_true",
+                    help="load the model at --out and time analytic against learned plans (plan_gain)")
+    ap.add_argument("--qubits", type=int, default=30, help="state size for --evaluate")
+    ap.add_argument("--seeds", default="100-109", help="circuit seeds for --evaluate, e.g. 100-109")
+    ap.add_argument("--workload", default="mixed", choices=("mixed", "entangling"))
     a = ap.parse_args(argv)
+    if a.evaluate:
+        lo, _, hi = a.seeds.partition("-")
+        net, _ = load(a.out)
+        r = plan_gain(net, seeds=range(int(lo), int(hi or lo) + 1), n=a.qubits, log=print, workload=a.workload)
+        print(json.dumps(r))
+        return
     if a.data:
         d = np.load(a.data)
         X, y, meta = d["X"], d["y"], json.loads(str(d["meta"]))

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cinttypes>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -87,16 +88,106 @@ std::string cim(const std::vector<std::pair<CF, std::string>>& t) {
 
 bool unit(CF c) { return c.re == 1.0f && c.im == 0.0f; }
 
+using cd = std::complex<double>;
+
 struct Gen {
   const ShmProgramV2& pg;
   std::ostringstream o;
   int nm[kRegAmps];  // register index j -> variable r<nm[j]>
   int phase = 0;
   std::string after_last_xchg;  // emitted once the last exchange has read the tile
+  // Deferred factors: variable r<v> holds its amplitude divided by pend[v].
+  // A diagonal factor on register bits only multiplies pend (no code).  A
+  // dense 2x2 or 4x4 product folds its inputs' factors into its constants
+  // and, when a later dense product of the same phase reads the output,
+  // divides the output row by its largest coefficient and keeps that
+  // coefficient in pend, so that term costs an add instead of a complex
+  // multiply.  Exchanges, the store and ops under a runtime condition
+  // first apply what is pending (one complex multiply per variable whose
+  // factor is not 1).  Scaling a row by one of its own coefficients leaves
+  // its rounding error bound unchanged.
+  bool defer = false;
+  bool dry = false;           // lookahead pass: records which outputs are read again
+  std::vector<char> consumed;  // per dense output, in order
+  int out_id = 0;
+  int last_out[kRegAmps];
+  cd pend[kRegAmps];
   explicit Gen(const ShmProgramV2& p) : pg(p) {
-    for (int j = 0; j < kRegAmps; ++j) nm[j] = j;
+    for (int j = 0; j < kRegAmps; ++j) {
+      nm[j] = j;
+      last_out[j] = -1;
+      pend[j] = 1.0;
+    }
   }
   std::string v(int j) const { return "r" + std::to_string(nm[j]); }
+
+  static CF cf_of(cd z) { return CF{(float)z.real(), (float)z.imag()}; }
+
+  // applies variable w's pending factor
+  void flush_var(int w) {
+    last_out[w] = -1;
+    const CF e = cf_of(pend[w]);
+    pend[w] = 1.0;
+    if (unit(e)) return;
+    const std::string x = "r" + std::to_string(w);
+    o << "{const float2 x=" << x << ";" << x << "=make_float2(" << cre({{e, "x"}}) << "," << cim({{e, "x"}})
+      << ");}\n";
+  }
+  void flush_all() {
+    for (int w = 0; w < kRegAmps; ++w) flush_var(w);
+  }
+
+  void diag(int j, CF e) {  // r_j *= e, a factor known at generation time
+    if (defer) pend[nm[j]] *= cd(e.re, e.im);
+    else mulc(j, e);
+  }
+
+  // r_idx[i] <- sum_k M[s*i + k] r_idx[k] for one group of s = 2 or 4
+  // registers; `cond`: the code sits under a runtime condition (the group's
+  // pending factors were applied before it, and its outputs keep factor 1)
+  void dense(const int* idx, int s, const CF* M, bool cond) {
+    int w[4];
+    for (int k = 0; k < s; ++k) w[k] = nm[idx[k]];
+    cd E[16];
+    for (int i = 0; i < s; ++i)
+      for (int k = 0; k < s; ++k) E[s * i + k] = cd(M[s * i + k].re, M[s * i + k].im) * pend[w[k]];
+    if (defer && !cond)
+      for (int k = 0; k < s; ++k)
+        if (last_out[w[k]] >= 0) consumed[last_out[w[k]]] = 1;
+    cd d[4];
+    int piv[4];
+    for (int i = 0; i < s; ++i) {
+      d[i] = 1.0;
+      piv[i] = -1;
+      if (!defer || cond) continue;
+      const int id = out_id++;
+      if (dry) consumed.push_back(0);
+      else if (id < (int)consumed.size() && consumed[id]) {
+        int kb = 0;
+        for (int k = 1; k < s; ++k)
+          if (std::abs(E[s * i + k]) > std::abs(E[s * i + kb])) kb = k;
+        if (std::abs(E[s * i + kb]) > 1e-30) {
+          d[i] = E[s * i + kb];
+          piv[i] = kb;
+        }
+      }
+    }
+    o << "{const float2 ";
+    for (int k = 0; k < s; ++k) o << (k ? "," : "") << "x" << k << "=" << v(idx[k]);
+    o << ";\n";
+    for (int i = 0; i < s; ++i) {
+      std::vector<std::pair<CF, std::string>> t;
+      if (piv[i] >= 0) t.push_back({CF{1.0f, 0.0f}, "x" + std::to_string(piv[i])});
+      for (int k = 0; k < s; ++k)
+        if (k != piv[i]) t.push_back({cf_of(E[s * i + k] / d[i]), "x" + std::to_string(k)});
+      o << v(idx[i]) << "=make_float2(" << cre(t) << "," << cim(t) << ");\n";
+    }
+    o << "}\n";
+    for (int i = 0; i < s; ++i) {
+      pend[w[i]] = d[i];
+      if (defer && !cond) last_out[w[i]] = out_id - s + i;
+    }
+  }
 
   // value (0/1) of a qubit reference that is not a register slot
   std::string known(uint32_t ref) const {
@@ -115,21 +206,19 @@ struct Gen {
       << cim({{e, "x"}}) << ");}\n";
   }
 
-  void g1(int t, CF u00, CF u01, CF u10, CF u11) {
+  void g1(int t, CF u00, CF u01, CF u10, CF u11, bool cond = false) {
+    const CF M[4] = {u00, u01, u10, u11};
     for (int j = 0; j < kRegAmps; ++j) {
       if (j & (1 << t)) continue;
-      int k = j | (1 << t);
-      std::string a = v(j), b = v(k);
-      o << "{const float2 x=" << a << ",y=" << b << ";" << a << "=make_float2("
-        << cre({{u00, "x"}, {u01, "y"}}) << "," << cim({{u00, "x"}, {u01, "y"}}) << ");" << b
-        << "=make_float2(" << cre({{u10, "x"}, {u11, "y"}}) << "," << cim({{u10, "x"}, {u11, "y"}})
-        << ");}\n";
+      const int idx[2] = {j, j | (1 << t)};
+      dense(idx, 2, M, cond);
     }
   }
 
   void swap_pair(int j, int k) { std::swap(nm[j], nm[k]); }
 
   void xchg(const PhaseMap& next, int next_index) {
+    flush_all();
     o << "__syncthreads();\n";
     const PhaseMap& cur = pg.maps[phase];
     for (int j = 0; j < kRegAmps; ++j) {
@@ -178,18 +267,16 @@ struct Gen {
         case PK_G1C: {
           CF u00 = cf(pc + 1), u01 = cf(pc + 3), u10 = cf(pc + 5), u11 = cf(pc + 7);
           if (B < (uint32_t)kRegBits) {
+            const CF M[4] = {u00, u01, u10, u11};
             for (int j = 0; j < kRegAmps; ++j) {
               if ((j & (1 << A)) || !((j >> B) & 1)) continue;
-              int k = j | (1 << A);
-              std::string a = v(j), b = v(k);
-              o << "{const float2 x=" << a << ",y=" << b << ";" << a << "=make_float2("
-                << cre({{u00, "x"}, {u01, "y"}}) << "," << cim({{u00, "x"}, {u01, "y"}}) << ");"
-                << b << "=make_float2(" << cre({{u10, "x"}, {u11, "y"}}) << ","
-                << cim({{u10, "x"}, {u11, "y"}}) << ");}\n";
+              const int idx[2] = {j, j | (1 << A)};
+              dense(idx, 2, M, false);
             }
           } else {
+            for (int j = 0; j < kRegAmps; ++j) flush_var(nm[j]);
             o << "if (" << known(B) << ") {\n";
-            g1((int)A, u00, u01, u10, u11);
+            g1((int)A, u00, u01, u10, u11, true);
             o << "}\n";
           }
           pc += 9;
@@ -206,6 +293,7 @@ struct Gen {
           pc += 1;
           break;
         case PK_XGK:
+          for (int j = 0; j < kRegAmps; ++j) flush_var(nm[j]);
           o << "if (" << known(B) << ") {\n";
           for (int j = 0; j < kRegAmps; ++j)
             if (!(j & (1 << A))) {
@@ -218,13 +306,13 @@ struct Gen {
         case PK_D1B: {
           CF e = cf(pc + 1);
           for (int j = 0; j < kRegAmps; ++j)
-            if (j & (1 << A)) mulc(j, e);
+            if (j & (1 << A)) diag(j, e);
           pc += 3;
           break;
         }
         case PK_D1: {
           CF e0 = cf(pc + 1), e1 = cf(pc + 3);
-          for (int j = 0; j < kRegAmps; ++j) mulc(j, (j & (1 << A)) ? e1 : e0);
+          for (int j = 0; j < kRegAmps; ++j) diag(j, (j & (1 << A)) ? e1 : e0);
           pc += 5;
           break;
         }
@@ -241,14 +329,14 @@ struct Gen {
         }
         case PK_D2: {
           CF d[4] = {cf(pc + 1), cf(pc + 3), cf(pc + 5), cf(pc + 7)};
-          for (int j = 0; j < kRegAmps; ++j) mulc(j, d[((j >> A) & 1) | (((j >> B) & 1) << 1)]);
+          for (int j = 0; j < kRegAmps; ++j) diag(j, d[((j >> A) & 1) | (((j >> B) & 1) << 1)]);
           pc += 9;
           break;
         }
         case PK_D2P: {
           CF e = cf(pc + 1);
           for (int j = 0; j < kRegAmps; ++j)
-            if (((j >> A) & 1) && ((j >> B) & 1)) mulc(j, e);
+            if (((j >> A) & 1) && ((j >> B) & 1)) diag(j, e);
           pc += 3;
           break;
         }
@@ -273,22 +361,18 @@ struct Gen {
           break;
         case PK_XX: {
           float c = word_f(w[pc + 1]), s = word_f(w[pc + 2]);
+          const CF M[4] = {CF{c, 0}, CF{0, -s}, CF{0, -s}, CF{c, 0}};
           for (int j = 0; j < kRegAmps; ++j) {
             if ((j >> B) & 1) continue;
-            int k = j ^ (1 << A) ^ (1 << B);
-            CF cc{c, 0}, ms{0, -s};
-            std::string a = v(j), b = v(k);
-            o << "{const float2 x=" << a << ",y=" << b << ";" << a << "=make_float2("
-              << cre({{cc, "x"}, {ms, "y"}}) << "," << cim({{cc, "x"}, {ms, "y"}}) << ");" << b
-              << "=make_float2(" << cre({{ms, "x"}, {cc, "y"}}) << "," << cim({{ms, "x"}, {cc, "y"}})
-              << ");}\n";
+            const int idx[2] = {j, j ^ (1 << A) ^ (1 << B)};
+            dense(idx, 2, M, false);
           }
           pc += 3;
           break;
         }
         case PK_SCALE: {
           CF e = cf(pc + 1);
-          for (int j = 0; j < kRegAmps; ++j) mulc(j, e);
+          for (int j = 0; j < kRegAmps; ++j) diag(j, e);
           pc += 3;
           break;
         }
@@ -298,14 +382,7 @@ struct Gen {
           for (int j = 0; j < kRegAmps; ++j) {
             if (((j >> A) & 1) || ((j >> B) & 1)) continue;
             const int idx[4] = {j, j | (1 << A), j | (1 << B), j | (1 << A) | (1 << B)};
-            o << "{const float2 x0=" << v(idx[0]) << ",x1=" << v(idx[1]) << ",x2=" << v(idx[2])
-              << ",x3=" << v(idx[3]) << ";\n";
-            for (int i = 0; i < 4; ++i) {
-              std::vector<std::pair<CF, std::string>> t;
-              for (int k = 0; k < 4; ++k) t.push_back({g[4 * i + k], "x" + std::to_string(k)});
-              o << v(idx[i]) << "=make_float2(" << cre(t) << "," << cim(t) << ");\n";
-            }
-            o << "}\n";
+            dense(idx, 4, g, false);
           }
           pc += 33;
           break;
@@ -346,6 +423,13 @@ static int prefetch_form() {
   const char* e = std::getenv("QSIM_JIT_PREFETCH");
   if (e && (e[0] == '0' || e[0] == '1' || e[0] == '2') && !e[1]) return e[0] - '0';
   return 0;
+}
+
+// Deferred factors in the generated code (Gen::defer): QSIM_JIT_DEFER = 0
+// turns them off.
+static bool defer_factors() {
+  const char* e = std::getenv("QSIM_JIT_DEFER");
+  return !(e && e[0] == '0' && !e[1]);
 }
 
 void jit_shape(const ShmProgramV2& pg, int* form, int* smem, int* min_blocks) {
@@ -441,8 +525,16 @@ bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::str
       g.after_last_xchg = "__syncthreads();\n" + issue;
     }
   }
+  if (defer_factors()) {
+    Gen look(pg);  // the lookahead pass: which dense outputs are read again
+    look.defer = look.dry = true;
+    if (!look.body()) return false;
+    g.defer = true;
+    g.consumed = std::move(look.consumed);
+  }
   if (!g.body()) return false;
   if (g.phase != (int)pg.maps.size() - 1) return false;
+  g.flush_all();
   o << "float2* __restrict__ op = psi + (base | pts);\n";
   {
     const PhaseMap& sm = pg.maps.back();
