@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
+#include <map>
 #include <sstream>
 #include <sys/stat.h>
 #include <thread>
@@ -59,6 +60,36 @@ std::string lin(const std::vector<std::pair<float, std::string>>& terms) {
       if (c == 1.0f) acc = "(" + acc + "+" + t.second + ")";
       else if (c == -1.0f) acc = "(" + acc + "-" + t.second + ")";
       else acc = "fmaf(" + flit(c) + "," + t.second + "," + acc + ")";
+    }
+  }
+  return acc.empty() ? std::string("0.0f") : acc;
+}
+
+// One real component of a sum of products whose coefficients are either
+// constants (c, a empty) or per-thread values (the expression a, added with
+// the sign of c = +-1).
+struct LT {
+  float c;
+  std::string a, x;
+};
+std::string lin_rt(const std::vector<LT>& terms) {
+  std::string acc;
+  for (const LT& t : terms) {
+    if (t.a.empty()) {
+      const float c = t.c;
+      if (c == 0.0f) continue;
+      if (acc.empty()) {
+        if (c == 1.0f) acc = t.x;
+        else if (c == -1.0f) acc = "(-" + t.x + ")";
+        else acc = "(" + flit(c) + "*" + t.x + ")";
+      } else {
+        if (c == 1.0f) acc = "(" + acc + "+" + t.x + ")";
+        else if (c == -1.0f) acc = "(" + acc + "-" + t.x + ")";
+        else acc = "fmaf(" + flit(c) + "," + t.x + "," + acc + ")";
+      }
+    } else {
+      const std::string c = t.c < 0 ? "(-" + t.a + ")" : t.a;
+      acc = acc.empty() ? "(" + c + "*" + t.x + ")" : "fmaf(" + c + "," + t.x + "," + acc + ")";
     }
   }
   return acc.empty() ? std::string("0.0f") : acc;
@@ -112,6 +143,21 @@ struct Gen {
   int out_id = 0;
   int last_out[kRegAmps];
   cd pend[kRegAmps];
+  // Runtime factors: a diagonal factor under a runtime condition (a control
+  // or phase on a thread or batch bit) becomes a per-thread select instead
+  // of a branch when the lookahead pass has seen a later dense product of
+  // the same phase read every variable it touches; rtf[v] then names the
+  // per-thread float2 by which r<v> must still be multiplied, and the
+  // product takes it into its coefficients (one complex product per
+  // coefficient and thread, not per amplitude).
+  std::string rtf[kRegAmps];
+  int nfac = 0;
+  std::map<std::string, std::string> fac_memo;  // expression -> declared factor variable
+  int rt_id = 0;                                // runtime diagonal ops, in order
+  std::vector<int> rt_open;                     // lookahead: variables of op id not yet read by a product
+  std::vector<int> rt_pend[kRegAmps];           // lookahead: op ids whose factor variable w still carries
+  std::vector<char> rt_ok;                      // op id may be deferred
+  bool rt_defer = false;
   explicit Gen(const ShmProgramV2& p) : pg(p) {
     for (int j = 0; j < kRegAmps; ++j) {
       nm[j] = j;
@@ -122,14 +168,64 @@ struct Gen {
   std::string v(int j) const { return "r" + std::to_string(nm[j]); }
 
   static CF cf_of(cd z) { return CF{(float)z.real(), (float)z.imag()}; }
+  static std::string cconst(CF c) { return "make_float2(" + flit(c.re) + "," + flit(c.im) + ")"; }
 
-  // applies variable w's pending factor
+  // a per-thread float2 holding `expr`, declared once in the batch loop
+  std::string fac(const std::string& expr) {
+    auto it = fac_memo.find(expr);
+    if (it != fac_memo.end()) return it->second;
+    const std::string name = "f" + std::to_string(nfac++);
+    o << "const float2 " << name << "=" << expr << ";\n";
+    fac_memo.emplace(expr, name);
+    return name;
+  }
+  // runtime factor f times the constant c
+  std::string fac_times(const std::string& f, CF c) {
+    if (unit(c)) return f;
+    return fac("make_float2(" + lin({{c.re, f + ".x"}, {-c.im, f + ".y"}}) + "," +
+               lin({{c.re, f + ".y"}, {c.im, f + ".x"}}) + ")");
+  }
+  void compose(int w, const std::string& f) {
+    if (rtf[w].empty()) rtf[w] = f;
+    else rtf[w] = fac("make_float2(" + rtf[w] + ".x*" + f + ".x-" + rtf[w] + ".y*" + f + ".y," + rtf[w] + ".x*" + f +
+                      ".y+" + rtf[w] + ".y*" + f + ".x)");
+  }
+
+  // Whether the next runtime diagonal op (touching registers with bit A =
+  // 0 and/or 1; A < 0: every register) is deferred.  The lookahead pass
+  // records the variables it touches; the real pass defers it when a dense
+  // product of the same phase read all of them before any flush.
+  bool runtime_diag(bool t0, bool t1, int A) {
+    if (!defer || !rt_defer) return false;
+    const int id = rt_id++;
+    if (dry) {
+      int cnt = 0;
+      for (int j = 0; j < kRegAmps; ++j)
+        if (A < 0 ? (t0 || t1) : (((j >> A) & 1) ? t1 : t0)) {
+          rt_pend[nm[j]].push_back(id);
+          ++cnt;
+        }
+      rt_open.push_back(cnt);
+      return false;
+    }
+    return id < (int)rt_ok.size() && rt_ok[id];
+  }
+
+  // applies variable w's pending factors
   void flush_var(int w) {
     last_out[w] = -1;
+    rt_pend[w].clear();
     const CF e = cf_of(pend[w]);
     pend[w] = 1.0;
-    if (unit(e)) return;
     const std::string x = "r" + std::to_string(w);
+    if (!rtf[w].empty()) {
+      const std::string c = fac_times(rtf[w], e);
+      rtf[w].clear();
+      o << "{const float2 x=" << x << ";" << x << "=make_float2(" << c << ".x*x.x-" << c << ".y*x.y," << c
+        << ".x*x.y+" << c << ".y*x.x);}\n";
+      return;
+    }
+    if (unit(e)) return;
     o << "{const float2 x=" << x << ";" << x << "=make_float2(" << cre({{e, "x"}}) << "," << cim({{e, "x"}})
       << ");}\n";
   }
@@ -152,8 +248,11 @@ struct Gen {
     for (int i = 0; i < s; ++i)
       for (int k = 0; k < s; ++k) E[s * i + k] = cd(M[s * i + k].re, M[s * i + k].im) * pend[w[k]];
     if (defer && !cond)
-      for (int k = 0; k < s; ++k)
+      for (int k = 0; k < s; ++k) {
         if (last_out[w[k]] >= 0) consumed[last_out[w[k]]] = 1;
+        for (int id : rt_pend[w[k]]) --rt_open[id];
+        rt_pend[w[k]].clear();
+      }
     cd d[4];
     int piv[4];
     for (int i = 0; i < s; ++i) {
@@ -163,28 +262,52 @@ struct Gen {
       const int id = out_id++;
       if (dry) consumed.push_back(0);
       else if (id < (int)consumed.size() && consumed[id]) {
-        int kb = 0;
-        for (int k = 1; k < s; ++k)
-          if (std::abs(E[s * i + k]) > std::abs(E[s * i + kb])) kb = k;
-        if (std::abs(E[s * i + kb]) > 1e-30) {
+        int kb = -1;  // the pivot: the largest coefficient known at generation time
+        for (int k = 0; k < s; ++k)
+          if (rtf[w[k]].empty() && (kb < 0 || std::abs(E[s * i + k]) > std::abs(E[s * i + kb]))) kb = k;
+        if (kb >= 0 && std::abs(E[s * i + kb]) > 1e-30) {
           d[i] = E[s * i + kb];
           piv[i] = kb;
         }
       }
     }
+    // coefficients that carry an input's runtime factor, declared before the block
+    std::string rc[16];
+    for (int i = 0; i < s; ++i)
+      for (int k = 0; k < s; ++k) {
+        const CF c = cf_of(E[s * i + k] / d[i]);
+        if (!rtf[w[k]].empty() && !(c.re == 0.0f && c.im == 0.0f)) rc[s * i + k] = fac_times(rtf[w[k]], c);
+      }
     o << "{const float2 ";
     for (int k = 0; k < s; ++k) o << (k ? "," : "") << "x" << k << "=" << v(idx[k]);
     o << ";\n";
     for (int i = 0; i < s; ++i) {
-      std::vector<std::pair<CF, std::string>> t;
-      if (piv[i] >= 0) t.push_back({CF{1.0f, 0.0f}, "x" + std::to_string(piv[i])});
+      std::vector<LT> re, im;
+      auto term = [&](int k) {
+        const std::string x = "x" + std::to_string(k);
+        if (!rc[s * i + k].empty()) {  // runtime coefficient c: (c.x xr - c.y xi, c.x xi + c.y xr)
+          const std::string& c = rc[s * i + k];
+          re.push_back({1.0f, c + ".x", x + ".x"});
+          re.push_back({-1.0f, c + ".y", x + ".y"});
+          im.push_back({1.0f, c + ".x", x + ".y"});
+          im.push_back({1.0f, c + ".y", x + ".x"});
+          return;
+        }
+        const CF c = k == piv[i] ? CF{1.0f, 0.0f} : cf_of(E[s * i + k] / d[i]);
+        re.push_back({c.re, "", x + ".x"});
+        re.push_back({-c.im, "", x + ".y"});
+        im.push_back({c.re, "", x + ".y"});
+        im.push_back({c.im, "", x + ".x"});
+      };
+      if (piv[i] >= 0) term(piv[i]);
       for (int k = 0; k < s; ++k)
-        if (k != piv[i]) t.push_back({cf_of(E[s * i + k] / d[i]), "x" + std::to_string(k)});
-      o << v(idx[i]) << "=make_float2(" << cre(t) << "," << cim(t) << ");\n";
+        if (k != piv[i]) term(k);
+      o << v(idx[i]) << "=make_float2(" << lin_rt(re) << "," << lin_rt(im) << ");\n";
     }
     o << "}\n";
     for (int i = 0; i < s; ++i) {
       pend[w[i]] = d[i];
+      if (!cond) rtf[w[i]].clear();
       if (defer && !cond) last_out[w[i]] = out_id - s + i;
     }
   }
@@ -318,11 +441,22 @@ struct Gen {
         }
         case PK_D1K: {
           CF d[4] = {cf(pc + 1), cf(pc + 3), cf(pc + 5), cf(pc + 7)};
-          for (int kb = 0; kb < 2; ++kb) {
-            if (unit(d[2 * kb]) && unit(d[2 * kb + 1])) continue;
-            o << "if (" << known(B) << (kb ? "" : " == 0u") << ") {\n";
-            for (int j = 0; j < kRegAmps; ++j) mulc(j, d[2 * kb + ((j >> A) & 1)]);
-            o << "}\n";
+          // register j takes d[2 kb + bit A of j], kb the known bit's value
+          bool touch[2];
+          for (int a = 0; a < 2; ++a) touch[a] = !(unit(d[a]) && unit(d[2 + a]));
+          if (runtime_diag(touch[0], touch[1], (int)A)) {
+            std::string f[2];
+            for (int a = 0; a < 2; ++a)
+              if (touch[a]) f[a] = fac("(" + known(B) + " ? " + cconst(d[2 + a]) + " : " + cconst(d[a]) + ")");
+            for (int j = 0; j < kRegAmps; ++j)
+              if (touch[(j >> A) & 1]) compose(nm[j], f[(j >> A) & 1]);
+          } else {
+            for (int kb = 0; kb < 2; ++kb) {
+              if (unit(d[2 * kb]) && unit(d[2 * kb + 1])) continue;
+              o << "if (" << known(B) << (kb ? "" : " == 0u") << ") {\n";
+              for (int j = 0; j < kRegAmps; ++j) mulc(j, d[2 * kb + ((j >> A) & 1)]);
+              o << "}\n";
+            }
           }
           pc += 9;
           break;
@@ -343,6 +477,18 @@ struct Gen {
         case PK_D0: {
           CF d[4] = {cf(pc + 1), cf(pc + 3), cf(pc + 5), cf(pc + 7)};
           std::string k0 = known(A), k1 = (B == REF_NONE) ? std::string("0u") : known(B);
+          bool any = false;  // a factor other than 1 for some value of the known bits
+          for (int idx = 0; idx < 4; ++idx)
+            if (!((Cu >> idx) & 1u) && !(B == REF_NONE && idx >= 2) && !unit(d[idx])) any = true;
+          if (any && runtime_diag(true, true, -1)) {
+            auto val = [&](int idx) { return ((Cu >> idx) & 1u) ? std::string("make_float2(1.0f,0.0f)") : cconst(d[idx]); };
+            std::string e = "(" + k0 + " ? " + val(1) + " : " + val(0) + ")";
+            if (B != REF_NONE) e = "(" + k1 + " ? (" + k0 + " ? " + val(3) + " : " + val(2) + ") : " + e + ")";
+            const std::string f = fac(e);
+            for (int j = 0; j < kRegAmps; ++j) compose(nm[j], f);
+            pc += 9;
+            break;
+          }
           for (int idx = 0; idx < 4; ++idx) {
             if ((Cu >> idx) & 1u) continue;
             if (B == REF_NONE && idx >= 2) continue;
@@ -426,10 +572,12 @@ static int prefetch_form() {
 }
 
 // Deferred factors in the generated code (Gen::defer): QSIM_JIT_DEFER = 0
-// turns them off.
-static bool defer_factors() {
+// turns them off, 1 keeps only the factors known at generation time, 2 (the
+// default) also defers runtime-conditioned diagonals (Gen::rt_defer).
+static int defer_factors() {
   const char* e = std::getenv("QSIM_JIT_DEFER");
-  return !(e && e[0] == '0' && !e[1]);
+  if (e && (e[0] == '0' || e[0] == '1') && !e[1]) return e[0] - '0';
+  return 2;
 }
 
 void jit_shape(const ShmProgramV2& pg, int* form, int* smem, int* min_blocks) {
@@ -525,12 +673,14 @@ bool jit_source(const ShmProgramV2& pg, int n, const std::string& name, std::str
       g.after_last_xchg = "__syncthreads();\n" + issue;
     }
   }
-  if (defer_factors()) {
+  if (const int level = defer_factors()) {
     Gen look(pg);  // the lookahead pass: which dense outputs are read again
     look.defer = look.dry = true;
+    look.rt_defer = g.rt_defer = level >= 2;
     if (!look.body()) return false;
     g.defer = true;
     g.consumed = std::move(look.consumed);
+    for (int c : look.rt_open) g.rt_ok.push_back(c == 0);
   }
   if (!g.body()) return false;
   if (g.phase != (int)pg.maps.size() - 1) return false;
