@@ -73,8 +73,16 @@ PARAMS = ([c + ("1",) for c in CASES] + [CASES[0] + ("2",), CASES[2] + ("2",), C
           + [CASES[1] + ("0",), CASES[3] + ("0",)])
 
 
+# and two whose store phase also keeps local bits 2 and 3 on lanes
+# (QSIM_STORE_SECTORS=0: a store-only exchange when they are register bits)
+PARAMS += [CASES[1] + ("1w",), CASES[3] + ("1w",)]
+
+
 @pytest.mark.parametrize("kind,n,make,smax,defer", PARAMS, ids=[f"{c[0]}-{c[1]}-defer{c[4]}" for c in PARAMS])
 def test_generated_source_matches_the_oracle(kind, n, make, smax, defer, tmp_path, monkeypatch):
+    if defer.endswith("w"):
+        monkeypatch.setenv("QSIM_STORE_SECTORS", "0")
+        defer = defer[:-1]
     monkeypatch.setenv("QSIM_JIT_DEFER", defer)
     g = make(n)
     plan = Q.Plan(n, g, algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=smax, precision=Q.QS_PREC_FP32)
