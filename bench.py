@@ -32,8 +32,10 @@ N_GATES = 5000
 SEED = 100
 # DRAM bytes per launch of the specialised shared-memory kernel as a fraction
 # of its algorithmic bytes, from an ncu capture of that kernel form at 28
-# qubits (kernel 10 of plan A: 2.148 GB read + 2.086 GB written for 4.295 GB
-# of one pass; None: not measured for the current form)
+# qubits (kernel 10 of plan A, deferred factors: 2.148 GB read + 2.086 GB
+# written for 4.295 GB of one pass; its generated code is the same under the
+# 32-B-sector store rule, which changes 13 of the 151 kernels at 30 qubits
+# and writes the same bytes; None: not measured for the current form)
 QSK_TRAFFIC_RATIO = 0.986
 WORKLOAD = (f"mixed circuit, {N_QUBITS} qubits, {N_GATES} gates from {{H,X,RX,RZ,CX,CZ,CP,SWAP}}, "
             f"partner distance 1+Geom(0.3), seed {SEED}; complex64 state 8 GiB")
