@@ -8,6 +8,7 @@ and known-bit branches -- on random input states, without a GPU; the GPU
 parity tests run the same source compiled by NVRTC."""
 import ctypes
 import os
+import re
 import shutil
 import subprocess
 
@@ -31,14 +32,15 @@ def _random_state(n, seed):
 
 def _build(plan, tmp_path, tag):
     """One shared library holding every kernel of the plan, each with a
-    host entry run_<k>(psi, nb, hi, nthr)."""
+    host entry run_<k>(psi, nb, hi, nthr).  A staged plan names its kernels
+    by their index within the stage, so every kernel is renamed hk<k>."""
     nk = plan.stats().num_kernels
     parts = [f'#include "{SHIM}"\n']
     for k in range(nk):
-        src = plan.kernel_source(k).replace(f"qsk{k}(", f"qsk{k}(", 1)
+        src = re.sub(r"\bqsk\d+", f"hk{k}", plan.kernel_source(k))
         parts.append(src)
         parts.append(f'extern "C" void run_{k}(float* psi, unsigned long long nb, unsigned long long hi, '
-                     f"unsigned nthr) {{ host_launch(qsk{k}, psi, nb, hi, nthr); }}\n")
+                     f"unsigned nthr) {{ host_launch(hk{k}, psi, nb, hi, nthr); }}\n")
     cpp = tmp_path / f"{tag}.cpp"
     so = tmp_path / f"{tag}.so"
     cpp.write_text("".join(parts))
@@ -115,3 +117,45 @@ def test_deferred_factors_remove_multiplies():
             del os.environ["QSIM_JIT_DEFER"]
         counts[defer] = src.count("fmaf(") + src.count("f*r") + src.count("f*x")
     assert counts["1"] < 0.85 * counts["0"], counts
+
+
+def test_staged_plan_sources_match_the_oracle(tmp_path):
+    """A staged plan's kernels run chunk by chunk as the host-staging loop
+    runs them: each stage sees the state with its local qubits first (in
+    ascending order) and its regional qubits above them, every chunk of 2^L
+    amplitudes is one launch view, and the chunk's regional bits reach the
+    kernel as hi = chunk << L (the known-bit values of regional controls and
+    phases)."""
+    n, L = 15, 12
+    g = C.mixed_circuit(n, 250, 21)
+    plan = Q.Plan(n, g, algo=Q.QS_ALGO_KERNELIZE, fuse_kmax=0, shm_max_active=10, local_qubits=L,
+                  precision=Q.QS_PREC_FP32)
+    stats = plan.stats()
+    assert stats.num_stages >= 2
+    lib = _build(plan, tmp_path, "staged")
+    psi0 = _random_state(n, 99)
+    st = psi0.astype(np.complex64)
+    idx = np.arange(1 << n)
+    regional_controls = 0
+    for si in range(stats.num_stages):
+        sd = plan.stage(si)
+        local = [q for q in range(n) if (sd["local_mask"] >> q) & 1]
+        order = local + [q for q in range(n) if not (sd["local_mask"] >> q) & 1]
+        logical = np.zeros_like(idx)
+        for p_, q in enumerate(order):
+            logical |= ((idx >> p_) & 1) << q
+        view = st[logical].view(np.float32).copy()
+        for k in range(sd["first_kernel"], sd["first_kernel"] + sd["num_kernels"]):
+            m = plan.kernel(k).nqubits
+            regional_controls += sum(int(b) >= L for b in re.findall(r"\(base \| hi\) >> (\d+)", plan.kernel_source(k)))
+            f = getattr(lib, f"run_{k}")
+            f.argtypes = [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_uint]
+            for c in range(1 << (n - L)):
+                chunk = view[2 * (c << L):2 * ((c + 1) << L)]
+                f(chunk.ctypes.data, 1 << (L - m), c << L, 1 << (m - 5))
+        st[logical] = view.view(np.complex64)
+    ref = sim.apply(n, g, psi0.copy())
+    got = st.astype(np.complex128)
+    assert regional_controls > 0  # some kernel reads a regional bit (one of the chunk's hi bits)
+    err = np.max(np.abs(got - ref))
+    assert err < 2e-5 * 2.0 ** (-n / 2) * len(g) ** 0.5, err
